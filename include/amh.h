@@ -1,0 +1,184 @@
+/*
+ * amh.h -- C-ABI of the GB300 (sm_103a) implementation of the AMHMVS
+ * red/black checkerboard update (Xu & Tao, "Multi-View Stereo with Asymmetric
+ * Checkerboard Propagation and Multi-Hypothesis Joint View Selection",
+ * arXiv 1805.07920).
+ *
+ * One context holds one reference view with up to 32 source views, all
+ * resident on one GPU.  Every step of the update runs in this library's own
+ * CUDA kernels; there is no CPU path.  The signatures use plain pointers and
+ * sizes only.
+ *
+ * Conventions shared by all entry points
+ *   - Return value: AMH_OK (0) on success, a negative AMH_E* code on failure.
+ *     No call aborts the process; amh_last_error() returns a message for the
+ *     last failure of a context (or of a failed amh_create when ctx is NULL).
+ *   - Images: uint8 grayscale, row-major, width x height, tightly packed.
+ *     Pixel (x, y) has its centre at integer coordinates (x, y).
+ *   - Cameras: pinhole K (3x3, last row 0 0 1), R (3x3), t (3), row-major,
+ *     world-to-camera: x_cam = R X_world + t (Sec. 2: calibrated cameras).
+ *   - Planes (Sec. 2, scene-space planes): per pixel (nx, ny, nz, D): unit
+ *     normal in reference-camera coordinates facing the camera (n . ray < 0)
+ *     and the z-depth D of the plane along the pixel's ray.
+ *   - Memory kinds: AMH_MEM_HOST buffers are ordinary host memory (pinned or
+ *     not); AMH_MEM_DEVICE buffers are device pointers on the context's GPU
+ *     (e.g. from torch.Tensor.data_ptr()).  The caller owns every buffer it
+ *     passes; the library copies inputs at create time and never keeps a
+ *     caller pointer.
+ *   - Streams: all work of a context is enqueued on its stream (the one given
+ *     at create time or by amh_set_stream; NULL = the legacy default stream).
+ *     Calls that take device buffers are asynchronous with respect to the
+ *     host; calls that take host buffers synchronise the stream before they
+ *     return.  A context must not be used from two host threads at once.
+ */
+#ifndef AMH_H
+#define AMH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(_WIN32)
+#define AMH_API
+#else
+#define AMH_API __attribute__((visibility("default")))
+#endif
+
+#define AMH_MAX_SRC 32
+
+enum {
+  AMH_OK = 0,
+  AMH_EINVAL = -1,      /* invalid argument (null pointer, size, camera, ...)   */
+  AMH_ECUDA = -2,       /* a CUDA runtime call failed                            */
+  AMH_ENOMEM = -3,      /* device or host allocation failed                      */
+  AMH_EDEVICE = -4,     /* a kernel reported an error through its status word   */
+  AMH_ESTATE = -5       /* call out of order (e.g. iterate before init)          */
+};
+
+enum { AMH_MEM_HOST = 0, AMH_MEM_DEVICE = 1 };
+
+/* parameter flags */
+enum {
+  AMH_FLAG_BILATERAL_SQUARED = 1  /* use dI^2 and dx^2 in the bilateral weight  */
+};
+
+typedef struct amh_ctx amh_ctx;
+
+typedef struct {
+  double K[9];
+  double R[9];
+  double t[3];
+  int32_t width;
+  int32_t height;
+} amh_camera;
+
+/* Method parameters.  amh_default_params() fills the values of Sec. 4:
+ * 6 iterations, tau_mc_init 0.8, alpha 90 (Eq. 2), beta 0.3 (Eq. 3),
+ * tau_up 1.2, n1 2, n2 3, k 4 (Sec. 3.2), sigma_I 3, sigma_x 30 (Eq. 8), and
+ * the 11x11 window with every other row and column (radius 5, stride 2,
+ * Sec. 3.3).  This build supports radius 5 / stride 2 only. */
+typedef struct {
+  int32_t iters;
+  float tau_mc_init, alpha, beta, tau_up;
+  int32_t n1, n2, k;
+  float sigma_I, sigma_x;
+  int32_t win_radius, win_stride;
+  float depth_min, depth_max;   /* range of random depths (init, refinement) */
+  uint64_t seed;                /* Philox4x32-10 key                          */
+  int32_t flags;                /* AMH_FLAG_*                                 */
+} amh_params;
+
+/* Per-pixel state, W x H arrays in the memory kind given to get/set:
+ *   plane[4 W H]  float  (nx, ny, nz, D) per pixel
+ *   cost[W H]     float  current unified cost m_final of the kept plane (Eq. 7)
+ *   sel[W H]      uint32 S_t: bit j set when source view j was a good view at
+ *                        the pixel's last update (Sec. 3.2)
+ *   vbest[W H]    uint8  v_t: most important view of the last update, 255 none
+ *   wmask[W H]    uint32 views with a nonzero weight psi_mod at the last update
+ *   choice[W H]   uint8  row that won the last update: 0..7 ACP region
+ *                        (near up/down/left/right, far up/down/left/right),
+ *                        8 own plane, 9 + c refinement candidate c
+ *   t             iteration index of the next update (0-based)
+ * Any pointer except plane may be NULL in amh_get_state (not read back) and
+ * in amh_set_state (left unchanged; plane is required there). */
+typedef struct {
+  float* plane;
+  float* cost;
+  uint32_t* sel;
+  uint8_t* vbest;
+  uint32_t* wmask;
+  uint8_t* choice;
+  int32_t t;
+} amh_state;
+
+/* Fill *out with the parameters of Sec. 4.  Returns AMH_EINVAL on NULL. */
+AMH_API int amh_default_params(amh_params* out);
+
+/* Create a context for reference view `ref` and source views src[0..n_src-1]
+ * (indices into cams/images, n_src in 1..32, no repeats, none equal to ref).
+ * images[v] points to a cams[v].height x cams[v].width uint8 image in the
+ * memory kind `images_mem`; only ref and the listed sources are read.  The
+ * images are copied into device-resident texture arrays.  Fails with
+ * AMH_EINVAL on bad sizes, singular or non-pinhole K, or unsupported window
+ * parameters; with AMH_ENOMEM when the device is full.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream). */
+AMH_API int amh_create(amh_ctx** out, const amh_params* params, int32_t n_views,
+                       const amh_camera* cams, const uint8_t* const* images,
+                       int32_t images_mem, int32_t ref, const int32_t* src,
+                       int32_t n_src, void* stream);
+
+/* Change the stream later work is enqueued on. */
+AMH_API int amh_set_stream(amh_ctx* ctx, void* stream);
+
+/* Random initialisation (Sec. 2, Gipuma-style random scene planes): depth
+ * uniform in [depth_min, depth_max], normal uniform on the sphere flipped to
+ * face the camera, from Philox4x32-10 draws keyed by (seed) with counter
+ * (pixel, 0, 0, 0); the initial cost is the mean of the k smallest per-view
+ * costs (the heuristic view selection of Sec. 2); S = {}, v = none, t = 0. */
+AMH_API int amh_init_random(amh_ctx* ctx);
+
+/* One colour phase of the red/black checkerboard (Sec. 3.1, Fig. 2(a)) at the
+ * current t: every pixel with (x + y) % 2 == color is updated from pixels of
+ * the other colour -- asymmetric checkerboard propagation (8 hypotheses),
+ * the 8 x N cost matrix of bilateral weighted NCC (Eqs. 1, 8), the
+ * multi-hypothesis joint view selection (Eqs. 2-6), the weighted best
+ * hypothesis (Eq. 7) and refinement (Sec. 3.3).  After color 1, t advances. */
+AMH_API int amh_step_phase(amh_ctx* ctx, int32_t color);
+
+/* k full iterations (black phase then red phase each). */
+AMH_API int amh_iterate(amh_ctx* ctx, int32_t k);
+
+/* Copy the state out / in (see amh_state). */
+AMH_API int amh_get_state(amh_ctx* ctx, amh_state* out, int32_t mem);
+AMH_API int amh_set_state(amh_ctx* ctx, const amh_state* in, int32_t mem);
+
+/* Read back the depth map (D), normals (3 floats per pixel), the cost and the
+ * selected-view masks (wmask).  Any pointer may be NULL. */
+AMH_API int amh_read_maps(amh_ctx* ctx, float* depth, float* normal3, float* cost,
+                          uint32_t* selected, int32_t mem);
+
+/* Reference size, number of sources, current t. */
+AMH_API int amh_get_info(const amh_ctx* ctx, int32_t* width, int32_t* height,
+                         int32_t* n_src, int32_t* t);
+
+/* Number of (hypothesis, view) cost evaluations the kernels have performed
+ * since the last reset (each is one 36-sample warped bilateral NCC).  The
+ * count is kept on the device; reading it synchronises the stream. */
+AMH_API int amh_pair_count(amh_ctx* ctx, uint64_t* count, int32_t reset);
+
+/* Wait for all work of the context; reports kernel status errors. */
+AMH_API int amh_synchronize(amh_ctx* ctx);
+
+/* Message of the last failure (never NULL). */
+AMH_API const char* amh_last_error(const amh_ctx* ctx);
+
+/* Free everything; NULL is allowed. */
+AMH_API void amh_destroy(amh_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMH_H */
