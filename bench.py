@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Throughput of the AMHMVS checkerboard update on GB300.
+
+One step = one whole depth map of the 3200x2112 reference with 10 source
+views: random initialisation + 6 iterations (12 colour phases: ACP, the 8 x N
+bilateral-NCC cost matrix, joint view selection, weighted choice and
+refinement), all in this repository's CUDA kernels through the C-ABI.
+
+Metric: Mpixel-iterations/s = W * H * 6 * steps * ranks / (max over ranks of
+the device time of the timed steps).  Multi-GPU runs give every rank its own
+reference view of the same 11-camera scene (independent depth maps, weak
+scaling, no collective on the data path).
+
+Printed: one JSON line with the value, the end-to-end figure through the
+C-ABI with host buffers (host->device image upload and device->host map
+read-back inside the timed region), the roofline of the dominant kernel
+(FP32 ALU bound), the FP64 oracle timed on the host cores as a reported CPU
+baseline, and the SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 oracle (the reference arm of this
+project: the paper ships no code) on a bounded crop of the same workload on
+the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+REPO = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, REPO)
+
+METRIC = "Mpixel-iterations/s (3200x2112, 10 src)"
+UNIT = "Mpx-iter/s"
+SCENE = "large"
+ITERS = 6
+SEED = 11
+# Algorithmic FP32 work of one (hypothesis, view) cost evaluation: 36 window
+# samples x 22 flop (3 homography, 2 perspective-divide multiplies, 11
+# bilinear, 6 moment flops) + 80 flop per pair (homography set-up, validity,
+# NCC from the moments).
+FLOP_PER_SAMPLE = 22
+SAMPLES_PER_PAIR = 36
+FLOP_PER_PAIR_SETUP = 80
+FLOP_PER_PAIR = SAMPLES_PER_PAIR * FLOP_PER_SAMPLE + FLOP_PER_PAIR_SETUP
+FP32_LANES_PER_SM = 128
+# dram__bytes_read.sum + dram__bytes_write.sum per phase launch from an ncu
+# capture, keyed by the hash of the kernel sources it was taken on (null
+# whenever the kernels changed since).
+KNOWN_TRAFFIC: dict[str, float] = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(REPO, "paper_1805_07920_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_setup(want_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if want_cuda else "gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons, n = [], [], set(), 0
+        for ln in out.splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            n += 1
+            for name, val in zip(self.NAMES, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def rank_scene(rank: int):
+    from paper_1805_07920_gb300 import synth
+    sc = synth.make_scene(SCENE)
+    if rank:
+        n = len(sc.cams)
+        ref = (sc.ref + rank) % n
+        src = sorted([v for v in range(n) if v != ref], key=lambda v: (abs(v - ref), v))
+        sc = synth.Scene(sc.name, sc.seed, sc.cams, sc.images, ref, src, sc.depth_min, sc.depth_max, {}, {})
+    return sc
+
+
+def cpu_oracle_rate(sc, seconds: float, crop=(320, 212)):
+    """FP64 oracle (single thread) on a centred crop of the reference with all
+    sources: init + iterations until `seconds` have passed."""
+    import oracle
+    from paper_1805_07920_gb300 import synth
+    oracle.build() if not os.path.exists(oracle.LIB_PATH) else None
+    w, h = crop
+    x0, y0 = (sc.width - w) // 2, (sc.height - h) // 2
+    c = synth.crop_scene(sc, x0, y0, w, h)
+    o = oracle.Oracle.from_scene(c, seed=SEED)
+    t0 = time.perf_counter()
+    o.init_random()
+    its = 0
+    while its < ITERS:
+        o.iterate(1)
+        its += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return w * h * its / dt / 1e6, dict(crop=f"{w}x{h}", iterations=its, seconds=round(dt, 2))
+
+
+def run_reference(args):
+    rank, world, _, pg = dist_setup(False)
+    if rank != 0:
+        return 0
+    sc = rank_scene(0)
+    crop = (160, 106)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, info = cpu_oracle_rate(sc, 0.0, crop=crop)   # init + 1 iteration
+        if i >= args.warmup:
+            vals.append(v)
+    val = float(np.mean(vals))
+    ms = crop[0] * crop[1] * 1 / (val * 1e6) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(sc),
+        "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: oracle init + 1 iteration on a {crop[0]}x{crop[1]} centred "
+                                   f"crop of the reference with all {len(sc.src)} full-size sources"},
+        "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(sc):
+    return {"workload": f"{SCENE}: {sc.width}x{sc.height} reference + {len(sc.src)} source views, "
+                        f"random init + {ITERS} checkerboard iterations",
+            "width": sc.width, "height": sc.height, "n_src": len(sc.src), "iterations": ITERS,
+            "window": "11x11 stride 2 (36 samples)",
+            "l2": "inputs larger than L2: ~280 MB resident per context (textures + state) vs 129 MB L2"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local, dist = dist_setup(True)
+    torch.cuda.set_device(local)
+    from paper_1805_07920_gb300 import amh
+    amh.lib()
+    sc = rank_scene(rank)
+    W, H = sc.width, sc.height
+    ctx = amh.Context.from_scene(sc, seed=SEED)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.init_random()
+        ctx.iterate(ITERS)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    ctx.synchronize()
+    # deterministic work per step: count the (hypothesis, view) evaluations once
+    ctx.pair_count(reset=True)
+    ctx.init_random()
+    pairs_init = ctx.pair_count(reset=True)
+    ctx.iterate(ITERS)
+    pairs_phase = ctx.pair_count(reset=True)
+
+    clock = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ph = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps * 2 * ITERS)]
+    ev0.record(stream)
+    k = 0
+    for _ in range(args.steps):
+        ctx.init_random()
+        for _it in range(ITERS):
+            for color in (0, 1):
+                ph[k][0].record(stream)
+                ctx.step_phase(color)
+                ph[k][1].record(stream)
+                k += 1
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    ms = ev0.elapsed_time(ev1)
+    phase_ms = float(np.mean([a.elapsed_time(b) for a, b in ph]))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = W * H * ITERS * args.steps * world / (ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the colour-phase kernel)
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks["sm_max_mhz"] or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flop_per_launch = pairs_phase / (2 * ITERS) * FLOP_PER_PAIR
+    achieved = flop_per_launch / (phase_ms / 1e3) / 1e12
+    khash = kernel_source_hash()
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": KNOWN_TRAFFIC.get(khash),
+                "kernel": "phase_kernel", "launch_ms": round(phase_ms, 3),
+                "flop_per_launch": flop_per_launch, "pairs_per_launch": pairs_phase / (2 * ITERS),
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                              f"(max SM clock)", "kernel_hash": khash}
+
+    # end to end through the C-ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = [torch.from_numpy(im).pin_memory() for im in sc.images]
+        host_imgs = [p.numpy() for p in pinned]
+        outs = {k2: torch.empty(s, dtype=torch.float32).pin_memory() for k2, s in
+                (("depth", (H, W)), ("normal", (H, W, 3)), ("cost", (H, W)))}
+        sel_out = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        h2d = int(sum(sc.images[v].nbytes for v in [sc.ref] + list(sc.src)))
+        d2h = int(sum(t.numel() * 4 for t in outs.values()) + sel_out.numel() * 4)
+
+        def e2e_step():
+            c = amh.Context(sc.cams, host_imgs, sc.ref, sc.src,
+                            amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=SEED))
+            c.init_random()
+            c.iterate(ITERS)
+            amh.lib().amh_read_maps(c.ctx, amh._ptr(outs["depth"].numpy()), amh._ptr(outs["normal"].numpy()),
+                                    amh._ptr(outs["cost"].numpy()), amh._ptr(sel_out.numpy()),
+                                    amh.AMH_MEM_HOST)
+            c.close()
+        e2e_step()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3
+        if dist:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": round(W * H * ITERS * args.e2e_steps * world / (e_ms / 1e3) / 1e6, 3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "path": "amh_create from pinned host images + init + 6 iterations + amh_read_maps to pinned "
+                       "host + amh_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = cpu_oracle_rate(sc, args.cpu_seconds)
+        cpu = {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle, one thread: init + {info['iterations']} iteration(s) on a {info['crop']} "
+                         f"centred crop of the reference with all {len(sc.src)} full-size sources "
+                         f"({info['seconds']} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ray-cast scene)",
+            "config": workload_config(sc) | {"parallelism": f"replicas{world}: one reference view per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": args.steps * (1 + 2 * ITERS),
+            "pairs_per_step": pairs_init + pairs_phase,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

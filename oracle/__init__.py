@@ -95,6 +95,8 @@ def lib():
         L.orc_refine_candidates.restype = ctypes.c_int
         L.orc_refine_candidates.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp]
         L.orc_random_plane.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp]
+        L.orc_score_plane.restype = ctypes.c_double
+        L.orc_score_plane.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp]
         _LIB = L
     return _LIB
 
@@ -270,6 +272,10 @@ class Oracle:
         out = np.zeros((6, 4), np.float64)
         n = lib().orc_refine_candidates(self.ctx, x, y, _ptr(pl), t, _ptr(out))
         return out[:n]
+
+    def score_plane(self, x, y, plane) -> float:
+        pl = np.ascontiguousarray(plane, np.float64)
+        return lib().orc_score_plane(self.ctx, x, y, _ptr(pl))
 
     def random_plane(self, x, y):
         out = np.zeros(4, np.float64)

@@ -525,26 +525,46 @@ static double weighted_cost(const orc_ctx* c, int x, int y, const double pl[4],
   return a / sw;
 }
 
-void orc_update_pixel(const orc_ctx* c, int x, int y, double out[4], double* cost_out,
-                      uint32_t* sel_out, int32_t* v_out, int32_t* choice_out) {
+/* Sec. 3.1 and Eqs. (1)-(6) for one pixel: the eight propagated rows, the
+ * cost matrix M and the view weights w (sum sw). */
+static void pixel_weights(const orc_ctx* c, int x, int y, double rows[][4], int* valid, double* M,
+                          double* w, double* sw, uint32_t* S, int32_t* v) {
   const int N = c->n_src;
   size_t pi = (size_t)y * c->W + x;
-  /* Sec. 3.1: eight propagated hypotheses */
-  double rows[ORC_NREGION][4];
-  int valid[ORC_NREGION];
-  double M[ORC_NREGION * ORC_MAX_SRC];
   for (int g = 0; g < ORC_NREGION; g++) {
     valid[g] = orc_acp_row(c, x, y, g, rows[g]);
     /* Eq. (1): m_gj for every source view */
     for (int j = 0; j < N; j++) M[g * N + j] = valid[g] ? orc_cost(c, x, y, rows[g], j) : 2.0;
   }
-  /* Eqs. (2)-(6): view weights */
+  orc_mhj(&c->p, c->t, M, valid, N, c->sel[pi], c->vprev[pi], w, S, v);
+  *sw = 0;
+  for (int j = 0; j < N; j++) *sw += w[j];
+}
+
+/* unified cost (Eq. 7) of an arbitrary plane at (x, y) under the weights this
+ * pixel's update would use -- for judging near-ties in parity checks */
+double orc_score_plane(const orc_ctx* c, int x, int y, const double plane[4]) {
+  double rows[ORC_NREGION][4], M[ORC_NREGION * ORC_MAX_SRC], w[ORC_MAX_SRC], sw;
+  int valid[ORC_NREGION];
+  uint32_t S;
+  int32_t v;
+  pixel_weights(c, x, y, rows, valid, M, w, &sw, &S, &v);
+  return weighted_cost(c, x, y, plane, w, sw);
+}
+
+void orc_update_pixel(const orc_ctx* c, int x, int y, double out[4], double* cost_out,
+                      uint32_t* sel_out, int32_t* v_out, int32_t* choice_out) {
+  const int N = c->n_src;
+  size_t pi = (size_t)y * c->W + x;
+  /* Sec. 3.1: eight propagated hypotheses; Eqs. (1)-(6): view weights */
+  double rows[ORC_NREGION][4];
+  int valid[ORC_NREGION];
+  double M[ORC_NREGION * ORC_MAX_SRC];
   double w[ORC_MAX_SRC];
   uint32_t S;
   int32_t v;
-  orc_mhj(&c->p, c->t, M, valid, N, c->sel[pi], c->vprev[pi], w, &S, &v);
-  double sw = 0;
-  for (int j = 0; j < N; j++) sw += w[j];
+  double sw;
+  pixel_weights(c, x, y, rows, valid, M, w, &sw, &S, &v);
   /* Eq. (7): unified cost; the pixel's own plane competes, winning ties */
   double best[4];
   memcpy(best, &c->plane[4 * pi], sizeof best);

@@ -85,6 +85,9 @@ void orc_iterate(orc_ctx* c, int k);
 void orc_update_pixel(const orc_ctx* c, int x, int y, double plane_out[4],
                       double* cost_out, uint32_t* sel_out, int32_t* v_out,
                       int32_t* choice_out);
+/* Unified cost (Eq. 7) of any plane at (x, y) under the view weights that
+ * pixel's update would use (for judging near-ties). */
+double orc_score_plane(const orc_ctx* c, int x, int y, const double plane[4]);
 /* Update only the listed pixels (all of one colour) and write them back. */
 void orc_update_pixels(orc_ctx* c, int n, const int32_t* xs, const int32_t* ys);
 

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C-ABI in ``include/amh.h`` (``_lib/libamh.so``).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels.  Host arrays are numpy arrays; device buffers are torch CUDA
+tensors (their ``data_ptr()`` is passed, and by default the context runs on
+torch's current stream).  There is no CPU fallback: if the library or a GPU is
+missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libamh.so")
+
+AMH_OK, AMH_EINVAL, AMH_ECUDA, AMH_ENOMEM, AMH_EDEVICE, AMH_ESTATE = 0, -1, -2, -3, -4, -5
+AMH_MEM_HOST, AMH_MEM_DEVICE = 0, 1
+AMH_FLAG_BILATERAL_SQUARED = 1
+MAX_SRC = 32
+
+EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_random",
+           "amh_step_phase", "amh_iterate", "amh_get_state", "amh_set_state", "amh_read_maps",
+           "amh_get_info", "amh_pair_count", "amh_synchronize", "amh_last_error", "amh_destroy"]
+
+
+class AmhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"amh error {code}: {msg}")
+        self.code = code
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_double * 9), ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("tau_mc_init", ctypes.c_float), ("alpha", ctypes.c_float),
+                ("beta", ctypes.c_float), ("tau_up", ctypes.c_float), ("n1", ctypes.c_int32),
+                ("n2", ctypes.c_int32), ("k", ctypes.c_int32), ("sigma_I", ctypes.c_float),
+                ("sigma_x", ctypes.c_float), ("win_radius", ctypes.c_int32), ("win_stride", ctypes.c_int32),
+                ("depth_min", ctypes.c_float), ("depth_max", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("flags", ctypes.c_int32)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("plane", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("sel", ctypes.c_void_p),
+                ("vbest", ctypes.c_void_p), ("wmask", ctypes.c_void_p), ("choice", ctypes.c_void_p),
+                ("t", ctypes.c_int32)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+
+
+def lib():
+    """Load ``libamh.so``; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.amh_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.amh_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Params), _i32, ctypes.POINTER(Camera),
+                                 ctypes.POINTER(_vp), _i32, _i32, ctypes.POINTER(_i32), _i32, _vp]
+        L.amh_set_stream.argtypes = [_vp, _vp]
+        L.amh_init_random.argtypes = [_vp]
+        L.amh_step_phase.argtypes = [_vp, _i32]
+        L.amh_iterate.argtypes = [_vp, _i32]
+        L.amh_get_state.argtypes = [_vp, ctypes.POINTER(State), _i32]
+        L.amh_set_state.argtypes = [_vp, ctypes.POINTER(State), _i32]
+        L.amh_read_maps.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32]
+        L.amh_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                   ctypes.POINTER(_i32)]
+        L.amh_pair_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _i32]
+        L.amh_synchronize.argtypes = [_vp]
+        L.amh_last_error.argtypes = [_vp]
+        L.amh_last_error.restype = ctypes.c_char_p
+        L.amh_destroy.argtypes = [_vp]
+        L.amh_destroy.restype = None
+        _LIB = L
+    return _LIB
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().amh_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_cameras(cams) -> ctypes.Array:
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].K[:] = [float(v) for v in np.asarray(c.K, float).ravel()]
+        arr[i].R[:] = [float(v) for v in np.asarray(c.R, float).ravel()]
+        arr[i].t[:] = [float(v) for v in np.asarray(c.t, float).ravel()]
+        arr[i].width, arr[i].height = int(c.width), int(c.height)
+    return arr
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_cuda and x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Context:
+    """One reference view and its sources on the GPU (``amh_create``)."""
+
+    def __init__(self, cams, images, ref: int, src, params: Params | None = None, stream=None):
+        L = lib()
+        self.params = params or default_params()
+        self._cams = make_cameras(cams)
+        n = len(cams)
+        dev = _is_torch(images[0])
+        self._keep = [im if dev else np.ascontiguousarray(im, np.uint8) for im in images]
+        for c, im in zip(cams, self._keep):
+            assert tuple(im.shape) == (c.height, c.width), "image shape must be (height, width)"
+        ptrs = (_vp * n)(*[(_ptr(im).value if im is not None else None) for im in self._keep])
+        srcs = (_i32 * len(src))(*[int(s) for s in src])
+        self.ctx = _vp()
+        if stream is None:
+            stream = _current_stream()
+        rc = L.amh_create(ctypes.byref(self.ctx), ctypes.byref(self.params), n, self._cams, ptrs,
+                          AMH_MEM_DEVICE if dev else AMH_MEM_HOST, int(ref), srcs, len(src), stream)
+        if rc != AMH_OK:
+            raise AmhError(rc, L.amh_last_error(None).decode())
+        self._keep = None
+        w, h, ns, t = _i32(), _i32(), _i32(), _i32()
+        L.amh_get_info(self.ctx, ctypes.byref(w), ctypes.byref(h), ctypes.byref(ns), ctypes.byref(t))
+        self.W, self.H, self.n_src = w.value, h.value, ns.value
+
+    @classmethod
+    def from_scene(cls, scene, params: Params | None = None, images=None, **kw):
+        p = params or default_params(depth_min=scene.depth_min, depth_max=scene.depth_max, **kw)
+        return cls(scene.cams, images if images is not None else scene.images, scene.ref, scene.src, p)
+
+    def _check(self, rc):
+        if rc != AMH_OK:
+            raise AmhError(rc, lib().amh_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            lib().amh_destroy(self.ctx)
+            self.ctx = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- method ----
+    def set_stream(self, stream):
+        self._check(lib().amh_set_stream(self.ctx, stream))
+
+    def init_random(self):
+        self._check(lib().amh_init_random(self.ctx))
+
+    def step_phase(self, color: int):
+        self._check(lib().amh_step_phase(self.ctx, int(color)))
+
+    def iterate(self, k: int):
+        self._check(lib().amh_iterate(self.ctx, int(k)))
+
+    def synchronize(self):
+        self._check(lib().amh_synchronize(self.ctx))
+
+    @property
+    def t(self) -> int:
+        t = _i32()
+        lib().amh_get_info(self.ctx, None, None, None, ctypes.byref(t))
+        return t.value
+
+    def pair_count(self, reset: bool = False) -> int:
+        c = ctypes.c_uint64()
+        self._check(lib().amh_pair_count(self.ctx, ctypes.byref(c), int(reset)))
+        return c.value
+
+    # ---- state ----
+    def get_state(self):
+        H, W = self.H, self.W
+        st = dict(plane=np.zeros((H, W, 4), np.float32), cost=np.zeros((H, W), np.float32),
+                  sel=np.zeros((H, W), np.uint32), vbest=np.zeros((H, W), np.uint8),
+                  wmask=np.zeros((H, W), np.uint32), choice=np.zeros((H, W), np.uint8))
+        s = State(*[_ptr(st[k]) for k in ("plane", "cost", "sel", "vbest", "wmask", "choice")], 0)
+        self._check(lib().amh_get_state(self.ctx, ctypes.byref(s), AMH_MEM_HOST))
+        st["t"] = s.t
+        return st
+
+    def get_state_device(self, out: dict):
+        """Copy the state into torch CUDA tensors given in ``out`` (any subset)."""
+        s = State(*[_ptr(out.get(k)) for k in ("plane", "cost", "sel", "vbest", "wmask", "choice")], 0)
+        self._check(lib().amh_get_state(self.ctx, ctypes.byref(s), AMH_MEM_DEVICE))
+        return s.t
+
+    def set_state(self, plane, cost=None, sel=None, vbest=None, wmask=None, choice=None, t=0):
+        dev = _is_torch(plane)
+        H, W = self.H, self.W
+
+        def conv(a, dt, shape):
+            if a is None:
+                return None
+            if dev:
+                return a.contiguous()
+            return np.ascontiguousarray(np.asarray(a).reshape(shape), dt)
+        arrs = [conv(plane, np.float32, (H, W, 4)), conv(cost, np.float32, (H, W)),
+                conv(sel, np.uint32, (H, W)), conv(vbest, np.uint8, (H, W)),
+                conv(wmask, np.uint32, (H, W)), conv(choice, np.uint8, (H, W))]
+        s = State(*[_ptr(a) for a in arrs], int(t))
+        self._check(lib().amh_set_state(self.ctx, ctypes.byref(s), AMH_MEM_DEVICE if dev else AMH_MEM_HOST))
+
+    def read_maps(self):
+        H, W = self.H, self.W
+        depth = np.zeros((H, W), np.float32)
+        normal = np.zeros((H, W, 3), np.float32)
+        cost = np.zeros((H, W), np.float32)
+        sel = np.zeros((H, W), np.uint32)
+        self._check(lib().amh_read_maps(self.ctx, _ptr(depth), _ptr(normal), _ptr(cost), _ptr(sel),
+                                        AMH_MEM_HOST))
+        return dict(depth=depth, normal=normal, cost=cost, selected=sel)
+
+    def read_maps_device(self, depth=None, normal=None, cost=None, selected=None):
+        self._check(lib().amh_read_maps(self.ctx, _ptr(depth), _ptr(normal), _ptr(cost), _ptr(selected),
+                                        AMH_MEM_DEVICE))

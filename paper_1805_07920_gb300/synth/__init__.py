@@ -308,9 +308,27 @@ SCENES = {"tiny": scene_tiny, "medium": scene_medium, "large": scene_large,
           "ring20": scene_ring20}
 
 
-def make_scene(name: str, seed: int | None = None) -> Scene:
+def make_scene(name: str, seed: int | None = None, cache_dir: str | None = None) -> Scene:
+    """Build a named scene.  With ``cache_dir`` (or $AMH_SCENE_CACHE) the
+    rendered scene is kept there as a pickle and reused."""
+    cache_dir = cache_dir or os.environ.get("AMH_SCENE_CACHE")
+    path = None
+    if cache_dir:
+        path = os.path.join(cache_dir, f"scene_{name}_{'default' if seed is None else seed}.pkl")
+        if os.path.exists(path):
+            import pickle
+            with open(path, "rb") as f:
+                return pickle.load(f)
     fn = SCENES[name]
-    return fn() if seed is None else fn(seed)
+    sc = fn() if seed is None else fn(seed)
+    if path:
+        import pickle
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp"
+        with open(tmp, "wb") as f:
+            pickle.dump(sc, f, protocol=pickle.HIGHEST_PROTOCOL)
+        os.replace(tmp, path)
+    return sc
 
 
 def crop_scene(scene: Scene, x0: int, y0: int, w: int, h: int) -> Scene:
