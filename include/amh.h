@@ -160,6 +160,34 @@ AMH_API int amh_set_state(amh_ctx* ctx, const amh_state* in, int32_t mem);
 AMH_API int amh_read_maps(amh_ctx* ctx, float* depth, float* normal3, float* cost,
                           uint32_t* selected, int32_t mem);
 
+/* Largest number of pixels amh_read_maps_noalloc moves per call. */
+#define AMH_NOALLOC_MAX_PIXELS 262144
+
+/* amh_read_maps without any allocation (the paper has no counterpart: this
+ * is a service for callers that cannot allocate device memory when they read
+ * results -- code running while a stream is captured into a CUDA graph,
+ * where allocation calls are not allowed; hosts whose pooling allocator owns
+ * the GPU and forbids other device allocations; loops that must not allocate
+ * after start-up).
+ *
+ * Copies the depth (float per pixel) and/or the normal (3 floats per pixel)
+ * of the pixels [first_pixel, first_pixel + n_pixels) in row-major order into
+ * HOST buffers of n_pixels (depth) and 3 * n_pixels (normal3) floats; either
+ * may be NULL, not both.  At most AMH_NOALLOC_MAX_PIXELS pixels per call
+ * (read larger maps in slices); more, or a range outside the image, returns
+ * AMH_EINVAL with a message and touches nothing.
+ *
+ * The data is staged through one fixed scratch array that is part of the
+ * library's device image (4 MB, held on every GPU that loads the library
+ * until the process exits); the call makes no cudaMalloc/cudaFree or other
+ * allocating call.  The first call on a device looks up the array's device
+ * address (once per device); make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose GPU work can
+ * overlap (other streams, other host threads) race on it, so serialise them.
+ * The call synchronises the context's stream before it returns. */
+AMH_API int amh_read_maps_noalloc(amh_ctx* ctx, float* depth, float* normal3,
+                                  int64_t first_pixel, int64_t n_pixels);
+
 /* Reference size, number of sources, current t. */
 AMH_API int amh_get_info(const amh_ctx* ctx, int32_t* width, int32_t* height,
                          int32_t* n_src, int32_t* t);

@@ -19,10 +19,12 @@ AMH_OK, AMH_EINVAL, AMH_ECUDA, AMH_ENOMEM, AMH_EDEVICE, AMH_ESTATE = 0, -1, -2, 
 AMH_MEM_HOST, AMH_MEM_DEVICE = 0, 1
 AMH_FLAG_BILATERAL_SQUARED = 1
 MAX_SRC = 32
+NOALLOC_MAX_PIXELS = 262144
 
 EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_random",
            "amh_step_phase", "amh_iterate", "amh_get_state", "amh_set_state", "amh_read_maps",
-           "amh_get_info", "amh_pair_count", "amh_synchronize", "amh_last_error", "amh_destroy"]
+           "amh_get_info", "amh_pair_count", "amh_synchronize", "amh_last_error", "amh_destroy",
+           "amh_read_maps_noalloc"]
 
 
 class AmhError(RuntimeError):
@@ -73,6 +75,7 @@ def lib():
         L.amh_get_state.argtypes = [_vp, ctypes.POINTER(State), _i32]
         L.amh_set_state.argtypes = [_vp, ctypes.POINTER(State), _i32]
         L.amh_read_maps.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32]
+        L.amh_read_maps_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64]
         L.amh_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                    ctypes.POINTER(_i32)]
         L.amh_pair_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _i32]
@@ -242,6 +245,14 @@ class Context:
         self._check(lib().amh_read_maps(self.ctx, _ptr(depth), _ptr(normal), _ptr(cost), _ptr(sel),
                                         AMH_MEM_HOST))
         return dict(depth=depth, normal=normal, cost=cost, selected=sel)
+
+    def read_maps_noalloc(self, depth=None, normal=None, first_pixel: int = 0, n_pixels: int | None = None):
+        """Depth/normal of a pixel range into host arrays, without any device
+        allocation (amh_read_maps_noalloc; at most NOALLOC_MAX_PIXELS)."""
+        if n_pixels is None:
+            n_pixels = self.W * self.H - first_pixel
+        self._check(lib().amh_read_maps_noalloc(self.ctx, _ptr(depth), _ptr(normal), int(first_pixel),
+                                                int(n_pixels)))
 
     def read_maps_device(self, depth=None, normal=None, cost=None, selected=None):
         self._check(lib().amh_read_maps(self.ctx, _ptr(depth), _ptr(normal), _ptr(cost), _ptr(selected),

@@ -14,6 +14,7 @@
 
 #include "amh.h"
 #include "amh_device.cuh"
+#include "amh_ctx.h"
 
 using namespace amh;
 
@@ -359,26 +360,7 @@ __global__ void split_maps_kernel(const float4* __restrict__ plane, size_t n, fl
 // ===========================================================================
 // host side
 // ===========================================================================
-struct amh_ctx {
-  amh_params p;
-  int W = 0, H = 0, N = 0, ref = 0;
-  int src[AMH_MAX_SRC];
-  cudaStream_t stream = nullptr;
-  cudaArray_t arr[AMH_MAX_SRC] = {};
-  cudaTextureObject_t tex[AMH_MAX_SRC] = {};
-  uint8_t* d_ref = nullptr;
-  float4* d_plane = nullptr;
-  float* d_cost = nullptr;
-  uint32_t* d_sel = nullptr;
-  uint8_t* d_vbest = nullptr;
-  uint32_t* d_wmask = nullptr;
-  uint8_t* d_choice = nullptr;
-  unsigned long long* d_pairs = nullptr;
-  PhaseArgs args;
-  int t = 0;
-  bool initialized = false;
-  std::string err;
-};
+// struct amh_ctx is defined in amh_ctx.h
 
 namespace {
 thread_local std::string g_create_err;

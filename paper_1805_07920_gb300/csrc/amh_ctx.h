@@ -1,0 +1,30 @@
+// amh_ctx.h -- the context behind the opaque amh_ctx handle of amh.h
+// (private to the library's translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "amh.h"
+#include "amh_device.cuh"
+
+struct amh_ctx {
+  amh_params p;
+  int W = 0, H = 0, N = 0, ref = 0;
+  int src[AMH_MAX_SRC];
+  cudaStream_t stream = nullptr;
+  cudaArray_t arr[AMH_MAX_SRC] = {};
+  cudaTextureObject_t tex[AMH_MAX_SRC] = {};
+  uint8_t* d_ref = nullptr;
+  float4* d_plane = nullptr;
+  float* d_cost = nullptr;
+  uint32_t* d_sel = nullptr;
+  uint8_t* d_vbest = nullptr;
+  uint32_t* d_wmask = nullptr;
+  uint8_t* d_choice = nullptr;
+  unsigned long long* d_pairs = nullptr;
+  amh::PhaseArgs args;
+  int t = 0;
+  bool initialized = false;
+  std::string err;
+};
