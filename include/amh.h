@@ -62,7 +62,11 @@ enum { AMH_MEM_HOST = 0, AMH_MEM_DEVICE = 1 };
 
 /* parameter flags */
 enum {
-  AMH_FLAG_BILATERAL_SQUARED = 1  /* use dI^2 and dx^2 in the bilateral weight  */
+  AMH_FLAG_BILATERAL_SQUARED = 1, /* use dI^2 and dx^2 in the bilateral weight  */
+  AMH_FLAG_IMAGES_F16 = 2         /* images are IEEE binary16 (2 bytes/pixel,
+                                     intensities in any unit) instead of uint8;
+                                     they are stored as FP16 textures, the
+                                     interpolation and NCC moments stay FP32   */
 };
 
 typedef struct amh_ctx amh_ctx;
@@ -160,7 +164,56 @@ AMH_API int amh_set_state(amh_ctx* ctx, const amh_state* in, int32_t mem);
 AMH_API int amh_read_maps(amh_ctx* ctx, float* depth, float* normal3, float* cost,
                           uint32_t* selected, int32_t mem);
 
-/* Largest number of pixels amh_read_maps_noalloc moves per call. */
+/* ------------------------------------------------------------------------
+ * Batched form.  The paper computes "the depth map for every reference image
+ * in turn" (Sec. 3, overview figure); here several references -- each with
+ * its own source list and its own image size -- are resident together and
+ * every colour phase of all of them is one persistent launch.  Reference r of
+ * a batch draws its random numbers with the key seed + r, so it reproduces a
+ * single-reference context created with that seed bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct amh_batch amh_batch;
+
+/* refs[0..n_refs-1] index cams/images (1..256 references); the sources of
+ * reference r are src_lists[src_offsets[r] .. src_offsets[r+1]-1]
+ * (src_offsets[0] = 0, 1..32 per reference, none equal to refs[r]).  Every
+ * view used is uploaded once (texture + linear copy).  stream NULL: the batch
+ * creates its own stream (CUDA graphs cannot be captured on the legacy
+ * default stream). */
+AMH_API int amh_batch_create(amh_batch** out, const amh_params* params, int32_t n_views,
+                             const amh_camera* cams, const uint8_t* const* images,
+                             int32_t images_mem, int32_t n_refs, const int32_t* refs,
+                             const int32_t* src_offsets, const int32_t* src_lists,
+                             void* stream);
+/* random initialisation of every reference (one launch; see amh_init_random) */
+AMH_API int amh_batch_init_random(amh_batch* batch);
+/* one colour phase of every reference (one persistent launch) */
+AMH_API int amh_batch_step_phase(amh_batch* batch, int32_t color);
+/* k iterations (2 launches each) */
+AMH_API int amh_batch_iterate(amh_batch* batch, int32_t k);
+/* initialisation + iters iterations replayed from a CUDA graph; the graph is
+ * captured on the first call for a given iters / tile variant and reused. */
+AMH_API int amh_batch_run(amh_batch* batch, int32_t iters);
+/* Tile variant of the phase kernel: 0 = 16 x 16, 1 = 32 x 8, 2 = 64 x 4
+ * pixels per block (8, 16 or 32 same-coloured pixels per row). */
+AMH_API int amh_batch_set_variant(amh_batch* batch, int32_t variant);
+/* Times initialisation + iters iterations with each tile variant on this
+ * batch and keeps the fastest; *chosen gets its index and ms_out[0..2] (may
+ * be NULL) the times.  The state afterwards is a tuning run: initialise
+ * again before use. */
+AMH_API int amh_batch_autotune(amh_batch* batch, int32_t iters, int32_t* chosen, float* ms_out);
+/* size and number of sources of reference r; *n_refs the batch size */
+AMH_API int amh_batch_info(const amh_batch* batch, int32_t r, int32_t* width, int32_t* height,
+                           int32_t* n_src, int32_t* n_refs);
+/* state of reference r (see amh_state) */
+AMH_API int amh_batch_get_state(amh_batch* batch, int32_t r, amh_state* out, int32_t mem);
+/* (hypothesis, view) evaluations since the last reset (see amh_pair_count) */
+AMH_API int amh_batch_pair_count(amh_batch* batch, uint64_t* count, int32_t reset);
+AMH_API int amh_batch_synchronize(amh_batch* batch);
+AMH_API const char* amh_batch_last_error(const amh_batch* batch);
+AMH_API void amh_batch_destroy(amh_batch* batch);
+
+
 #define AMH_NOALLOC_MAX_PIXELS 262144
 
 /* amh_read_maps without any allocation (the paper has no counterpart: this

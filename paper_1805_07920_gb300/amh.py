@@ -18,13 +18,17 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 AMH_OK, AMH_EINVAL, AMH_ECUDA, AMH_ENOMEM, AMH_EDEVICE, AMH_ESTATE = 0, -1, -2, -3, -4, -5
 AMH_MEM_HOST, AMH_MEM_DEVICE = 0, 1
 AMH_FLAG_BILATERAL_SQUARED = 1
+AMH_FLAG_IMAGES_F16 = 2
 MAX_SRC = 32
 NOALLOC_MAX_PIXELS = 262144
 
 EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_random",
            "amh_step_phase", "amh_iterate", "amh_get_state", "amh_set_state", "amh_read_maps",
            "amh_get_info", "amh_pair_count", "amh_synchronize", "amh_last_error", "amh_destroy",
-           "amh_read_maps_noalloc"]
+           "amh_read_maps_noalloc", "amh_batch_create", "amh_batch_init_random", "amh_batch_step_phase",
+           "amh_batch_iterate", "amh_batch_run", "amh_batch_set_variant", "amh_batch_autotune",
+           "amh_batch_info", "amh_batch_get_state", "amh_batch_pair_count", "amh_batch_synchronize",
+           "amh_batch_last_error", "amh_batch_destroy"]
 
 
 class AmhError(RuntimeError):
@@ -131,7 +135,10 @@ def _current_stream():
 
 
 class Context:
-    """One reference view and its sources on the GPU (``amh_create``)."""
+    """One reference view and its sources on the GPU (``amh_create``).
+
+    ``images`` are uint8 or float16 arrays (numpy on the host or torch on the
+    GPU); float16 images select the FP16 texture storage."""
 
     def __init__(self, cams, images, ref: int, src, params: Params | None = None, stream=None):
         L = lib()
@@ -139,7 +146,11 @@ class Context:
         self._cams = make_cameras(cams)
         n = len(cams)
         dev = _is_torch(images[0])
-        self._keep = [im if dev else np.ascontiguousarray(im, np.uint8) for im in images]
+        half = str(images[0].dtype).endswith("float16")
+        if half:
+            self.params.flags |= AMH_FLAG_IMAGES_F16
+        dt = np.float16 if half else np.uint8
+        self._keep = [im if dev else np.ascontiguousarray(im, dt) for im in images]
         for c, im in zip(cams, self._keep):
             assert tuple(im.shape) == (c.height, c.width), "image shape must be (height, width)"
         ptrs = (_vp * n)(*[(_ptr(im).value if im is not None else None) for im in self._keep])
@@ -257,3 +268,123 @@ class Context:
     def read_maps_device(self, depth=None, normal=None, cost=None, selected=None):
         self._check(lib().amh_read_maps(self.ctx, _ptr(depth), _ptr(normal), _ptr(cost), _ptr(selected),
                                         AMH_MEM_DEVICE))
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+_BATCH_READY = False
+
+
+def _batch_lib():
+    global _BATCH_READY
+    L = lib()
+    if not _BATCH_READY:
+        L.amh_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Params), _i32, ctypes.POINTER(Camera),
+                                       ctypes.POINTER(_vp), _i32, _i32, ctypes.POINTER(_i32),
+                                       ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp]
+        for name in ("amh_batch_init_random", "amh_batch_synchronize"):
+            getattr(L, name).argtypes = [_vp]
+        L.amh_batch_step_phase.argtypes = [_vp, _i32]
+        L.amh_batch_iterate.argtypes = [_vp, _i32]
+        L.amh_batch_run.argtypes = [_vp, _i32]
+        L.amh_batch_set_variant.argtypes = [_vp, _i32]
+        L.amh_batch_autotune.argtypes = [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)]
+        L.amh_batch_info.argtypes = [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                     ctypes.POINTER(_i32)]
+        L.amh_batch_get_state.argtypes = [_vp, _i32, ctypes.POINTER(State), _i32]
+        L.amh_batch_pair_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _i32]
+        L.amh_batch_last_error.argtypes = [_vp]
+        L.amh_batch_last_error.restype = ctypes.c_char_p
+        L.amh_batch_destroy.argtypes = [_vp]
+        L.amh_batch_destroy.restype = None
+        _BATCH_READY = True
+    return L
+
+
+class Batch:
+    """Several references at once (``amh_batch_create``): refs[r] with the
+    sources src_lists[r]."""
+
+    def __init__(self, cams, images, refs, src_lists, params: Params | None = None, stream=None):
+        L = _batch_lib()
+        self.params = params or default_params()
+        self._cams = make_cameras(cams)
+        n = len(cams)
+        half = str(images[0].dtype).endswith("float16")
+        if half:
+            self.params.flags |= AMH_FLAG_IMAGES_F16
+        dt = np.float16 if half else np.uint8
+        keep = [np.ascontiguousarray(im, dt) for im in images]
+        ptrs = (_vp * n)(*[k.ctypes.data for k in keep])
+        offs = [0]
+        flat = []
+        for s in src_lists:
+            flat += [int(v) for v in s]
+            offs.append(len(flat))
+        self.ctx = _vp()
+        rc = L.amh_batch_create(ctypes.byref(self.ctx), ctypes.byref(self.params), n, self._cams, ptrs,
+                                AMH_MEM_HOST, len(refs), (_i32 * len(refs))(*refs), (_i32 * len(offs))(*offs),
+                                (_i32 * len(flat))(*flat), stream)
+        if rc != AMH_OK:
+            raise AmhError(rc, L.amh_batch_last_error(None).decode())
+        self.n_refs = len(refs)
+        self.sizes = []
+        for r in range(self.n_refs):
+            w, h, ns = _i32(), _i32(), _i32()
+            L.amh_batch_info(self.ctx, r, ctypes.byref(w), ctypes.byref(h), ctypes.byref(ns), None)
+            self.sizes.append((w.value, h.value, ns.value))
+
+    def _check(self, rc):
+        if rc != AMH_OK:
+            raise AmhError(rc, _batch_lib().amh_batch_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            _batch_lib().amh_batch_destroy(self.ctx)
+            self.ctx = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_random(self):
+        self._check(_batch_lib().amh_batch_init_random(self.ctx))
+
+    def step_phase(self, color):
+        self._check(_batch_lib().amh_batch_step_phase(self.ctx, int(color)))
+
+    def iterate(self, k):
+        self._check(_batch_lib().amh_batch_iterate(self.ctx, int(k)))
+
+    def run(self, iters):
+        self._check(_batch_lib().amh_batch_run(self.ctx, int(iters)))
+
+    def set_variant(self, v):
+        self._check(_batch_lib().amh_batch_set_variant(self.ctx, int(v)))
+
+    def autotune(self, iters=1):
+        ch = _i32()
+        ms = (ctypes.c_float * 3)()
+        self._check(_batch_lib().amh_batch_autotune(self.ctx, int(iters), ctypes.byref(ch), ms))
+        return ch.value, list(ms)
+
+    def synchronize(self):
+        self._check(_batch_lib().amh_batch_synchronize(self.ctx))
+
+    def pair_count(self, reset=False):
+        c = ctypes.c_uint64()
+        self._check(_batch_lib().amh_batch_pair_count(self.ctx, ctypes.byref(c), int(reset)))
+        return c.value
+
+    def get_state(self, r):
+        W, H, _ = self.sizes[r]
+        st = dict(plane=np.zeros((H, W, 4), np.float32), cost=np.zeros((H, W), np.float32),
+                  sel=np.zeros((H, W), np.uint32), vbest=np.zeros((H, W), np.uint8),
+                  wmask=np.zeros((H, W), np.uint32), choice=np.zeros((H, W), np.uint8))
+        s = State(*[_ptr(st[k]) for k in ("plane", "cost", "sel", "vbest", "wmask", "choice")], 0)
+        self._check(_batch_lib().amh_batch_get_state(self.ctx, int(r), ctypes.byref(s), AMH_MEM_HOST))
+        st["t"] = s.t
+        return st

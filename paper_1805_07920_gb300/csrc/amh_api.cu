@@ -1,8 +1,7 @@
-// amh_api.cu -- the C-ABI of include/amh.h and the kernels of the
-// checkerboard update: random initialisation, one colour phase (ACP + cost
-// matrix + joint view selection + weighted choice + refinement) and the map
-// read-back.  All method arithmetic runs in the kernels below; the host code
-// validates arguments, converts the cameras once (in FP64) and launches.
+// amh_api.cu -- the C-ABI of include/amh.h (host side).  It validates
+// arguments, converts the cameras once (in FP64), uploads the source views as
+// textures and launches the kernels of amh_kernels.cu; all method arithmetic
+// runs in those kernels.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -15,337 +14,11 @@
 #include "amh.h"
 #include "amh_device.cuh"
 #include "amh_ctx.h"
+#include "amh_kernels.h"
 
 using namespace amh;
 
-// ===========================================================================
-// Sec. 3.1: the eight ACP regions.  Near V-shaped regions (7 candidates): the
-// axis pixel at distance 1 and the pairs at lateral offset +-a, distance a+1;
-// far strips (11 candidates): the axis pixels at distances 3, 5, ..., 23.
-// Scan order nearest first, negative lateral side first; every offset has odd
-// |dx| + |dy| (opposite checkerboard colour).
-// ===========================================================================
-namespace {
-// candidate c of the 72: regions 0..3 hold 7 each, regions 4..7 hold 11 each
-__host__ __device__ constexpr int acp_region(int c) { return c < 28 ? c / 7 : 4 + (c - 28) / 11; }
-__host__ __device__ constexpr int acp_index(int c) { return c < 28 ? c % 7 : (c - 28) % 11; }
-__host__ __device__ constexpr int acp_start(int g) { return g < 4 ? 7 * g : 28 + 11 * (g - 4); }
-// axis distance and signed lateral offset of candidate c
-__host__ __device__ constexpr int acp_depth(int c) {
-  return acp_region(c) < 4 ? (acp_index(c) + 1) / 2 + 1 : 3 + 2 * acp_index(c);
-}
-__host__ __device__ constexpr int acp_lateral(int c) {
-  return acp_region(c) < 4 && acp_index(c) > 0 ? ((acp_index(c) & 1) ? -1 : 1) * ((acp_index(c) + 1) / 2) : 0;
-}
-// directions: up (0,-1), down (0,1), left (-1,0), right (1,0); the lateral
-// axis is x for up/down and y for left/right
-__host__ __device__ constexpr int acp_dx(int c) {
-  return (acp_region(c) & 3) == 2 ? -acp_depth(c) : (acp_region(c) & 3) == 3 ? acp_depth(c) : acp_lateral(c);
-}
-__host__ __device__ constexpr int acp_dy(int c) {
-  return (acp_region(c) & 3) == 0 ? -acp_depth(c) : (acp_region(c) & 3) == 1 ? acp_depth(c) : acp_lateral(c);
-}
-static_assert(acp_dx(0) == 0 && acp_dy(0) == -1, "near up starts at (0, -1)");
-static_assert(acp_dx(1) == -1 && acp_dy(1) == -2 && acp_dx(2) == 1 && acp_dy(2) == -2, "V arms");
-static_assert(acp_dx(6) == 3 && acp_dy(6) == -4, "near up ends at (3, -4)");
-static_assert(acp_dx(7 * 2 + 1) == -2 && acp_dy(7 * 2 + 1) == -1, "near left (-2, -1)");
-static_assert(acp_dx(28) == 0 && acp_dy(28) == -3 && acp_dy(38) == -23, "far up strip 3..23");
-static_assert(acp_dx(71) == 23 && acp_dy(71) == 0, "far right ends at (23, 0)");
-}  // namespace
-
 namespace amh {
-
-// ---------------------------------------------------------------------------
-// Refinement candidates (Sec. 3.3).  rho_t = 2^-(t+1) halves every iteration;
-// the bisection candidate perturbs depth and normal; from t = 3 on the five
-// other combinations of {own, perturbed, random} depth and normal follow:
-// (random D, n), (D, random n), (random D, random n), (perturbed D, n),
-// (D, perturbed n).  Draws (pixel, t, 0, 1) and (pixel, t, 1, 1).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int refine_candidates(const PhaseArgs& a, int x, int y, float4 pl,
-                                                 float3 ray, float4* cand) {
-  const uint32_t pix = (uint32_t)(y * a.W + x);
-  const float rho = ldexpf(1.f, -(a.t + 1));
-  const uint4 r0 = philox4x32_10(make_uint4(pix, (uint32_t)a.t, 0u, 1u), a.key0, a.key1);
-  const float Dp = pl.w * (1.f + rho * (2.f * u01(r0.x) - 1.f));
-  float3 np = make_float3(pl.x + rho * (2.f * u01(r0.y) - 1.f), pl.y + rho * (2.f * u01(r0.z) - 1.f),
-                          pl.z + rho * (2.f * u01(r0.w) - 1.f));
-  const float inn = 1.f / sqrtf(dot3(np, np));
-  np = face_camera(make_float3(np.x * inn, np.y * inn, np.z * inn), ray);
-  cand[0] = make_float4(np.x, np.y, np.z, Dp);
-  if (a.t < 3) return 1;
-  const uint4 r1 = philox4x32_10(make_uint4(pix, (uint32_t)a.t, 1u, 1u), a.key0, a.key1);
-  const float Dr = a.dmin + (a.dmax - a.dmin) * u01(r1.x);
-  const float3 nr = face_camera(normal_from_uniforms(u01(r1.y), u01(r1.z)), ray);
-  cand[1] = make_float4(pl.x, pl.y, pl.z, Dr);
-  cand[2] = make_float4(nr.x, nr.y, nr.z, pl.w);
-  cand[3] = make_float4(nr.x, nr.y, nr.z, Dr);
-  cand[4] = make_float4(pl.x, pl.y, pl.z, Dp);
-  cand[5] = make_float4(np.x, np.y, np.z, pl.w);
-  return 6;
-}
-
-// ---------------------------------------------------------------------------
-// Eqs. (2)-(6): weights of the N views from the 8 x N cost matrix M (rows of
-// invalid regions are left out of the counts and of the mean of Eq. (4)).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void joint_view_selection(const PhaseArgs& a, const float* M, uint32_t valid,
-                                                     uint32_t S_prev, int v_prev, float* w,
-                                                     uint32_t* S_out, int* v_out) {
-  const int N = a.N;
-  const int nvalid = __popc(valid);
-  const int k = a.k < N ? a.k : N;
-  uint32_t S = 0;
-  float psim[kMaxSrc];
-  for (int j = 0; j < N; j++) {
-    int ng = 0, nb = 0;
-    float psi = 0.f;
-#pragma unroll
-    for (int i = 0; i < kRegions; i++) {
-      if (!(valid >> i & 1u)) continue;
-      const float m = M[i * kMaxSrc + j];
-      ng += m < a.tau;
-      nb += m > a.tau_up;
-      psi += expf(-m * m * a.inv2beta2);          // Eq. (3)
-    }
-    psim[j] = 0.f;
-    if (ng > a.n1 && nb < a.n2) {                  // good view
-      S |= 1u << j;
-      psi = psi / (float)nvalid;                   // Eq. (4)
-      psim[j] = (j == v_prev) ? 2.f * psi : psi;   // Eqs. (5), (6)
-    }
-  }
-  int v = -1;
-  for (int j = 0; j < N; j++) {
-    float wj = 0.f;
-    if (S >> j & 1u) {
-      int rank = 0;
-      for (int q = 0; q < N; q++)
-        rank += (S >> q & 1u) && (psim[q] > psim[j] || (psim[q] == psim[j] && q < j));
-      if (rank < k) wj = psim[j];                  // at most k views keep weight
-      if (rank == 0) v = j;
-    } else if (S_prev >> j & 1u) {
-      wj = 0.2f;                                   // dropped since t - 1, Eq. (5)
-    }
-    w[j] = wj;
-  }
-  float sw = 0.f;
-  for (int j = 0; j < N; j++) sw += w[j];
-  if (sw == 0.f) {  // no view at all: the k views of smallest mean cost
-    float cm[kMaxSrc];
-    for (int j = 0; j < N; j++) {
-      float s = 0.f;
-#pragma unroll
-      for (int i = 0; i < kRegions; i++)
-        if (valid >> i & 1u) s += M[i * kMaxSrc + j];
-      cm[j] = nvalid ? s / (float)nvalid : 0.f;
-    }
-    for (int j = 0; j < N; j++) {
-      int rank = 0;
-      for (int q = 0; q < N; q++) rank += cm[q] < cm[j] || (cm[q] == cm[j] && q < j);
-      w[j] = rank < k ? 1.f : 0.f;
-    }
-  }
-  *S_out = S;
-  *v_out = v;
-}
-
-// cost of one plane under the weights w (Eq. 7), views with w = 0 skipped
-__device__ __forceinline__ float weighted_cost(const PhaseArgs& a, const Hyp& h, float fx, float fy,
-                                               const RefWin& rw, const float* w, float inv_sw,
-                                               int* npairs) {
-  float acc = 0.f;
-  for (int j = 0; j < a.N; j++) {
-    const float wj = w[j];
-    if (wj > 0.f) {
-      int ev = 0;
-      acc = fmaf(wj, ncc_cost(a.v[j], h, fx, fy, rw, &ev), acc);
-      *npairs += ev;
-    }
-  }
-  return acc * inv_sw;
-}
-
-// ---------------------------------------------------------------------------
-// One pixel's checkerboard update.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void update_pixel(const PhaseArgs& a, int x, int y, int* npairs) {
-  const size_t pi = (size_t)y * a.W + x;
-  const float fx = (float)x, fy = (float)y;
-  const float3 ray = ref_ray(a.Kinv, fx, fy);
-
-  // --- Sec. 3.1: asymmetric checkerboard propagation -----------------------
-  int pick[kRegions];
-#pragma unroll
-  for (int g = 0; g < kRegions; g++) {
-    int best = -1;
-    float bc = 0.f;
-#pragma unroll
-    for (int c = acp_start(g); c < acp_start(g + 1); c++) {
-      const int qx = x + acp_dx(c), qy = y + acp_dy(c);
-      if (qx < 0 || qy < 0 || qx >= a.W || qy >= a.H) continue;
-      const int q = qy * a.W + qx;
-      const float cq = __ldg(&a.cost[q]);
-      if (best < 0 || cq < bc) { best = q; bc = cq; }
-    }
-    pick[g] = best;
-  }
-  float4 hpl[kRegions];
-  float3 hc[kRegions];
-  uint32_t valid = 0;
-#pragma unroll
-  for (int g = 0; g < kRegions; g++) {
-    hpl[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    hc[g] = make_float3(0.f, 0.f, 0.f);
-    if (pick[g] < 0) continue;
-    const int q = pick[g];
-    const float4 pq = a.plane[q];
-    const float3 nq = make_float3(pq.x, pq.y, pq.z);
-    const float3 rq = ref_ray(a.Kinv, (float)(q % a.W), (float)(q / a.W));
-    const float d = -pq.w * dot3(nq, rq);        // plane offset, same for q and x
-    const float den = dot3(nq, ray);
-    if (!(den < 0.f)) continue;
-    const float Dx = -d / den;
-    if (!(Dx > 0.f) || !isfinite(Dx)) continue;
-    const Hyp h = make_hyp(a.Kinv, make_float4(nq.x, nq.y, nq.z, Dx), ray);
-    if (!h.ok) continue;
-    hpl[g] = h.pl;
-    hc[g] = h.c;
-    valid |= 1u << g;
-  }
-
-  // --- reference window -----------------------------------------------------
-  RefWin rw;
-  load_ref_window(a, x, y, rw);
-
-  // --- Eq. (1): the 8 x N cost matrix ---------------------------------------
-  float M[kRegions * kMaxSrc];
-  for (int j = 0; j < a.N; j++) {
-    const ViewConst& V = a.v[j];
-#pragma unroll 1
-    for (int g = 0; g < kRegions; g++) {
-      float m = kWorst;
-      if (valid >> g & 1u) {
-        Hyp h;
-        h.pl = hpl[g];
-        h.c = hc[g];
-        h.ok = true;
-        int ev = 0;
-        m = ncc_cost(V, h, fx, fy, rw, &ev);
-        *npairs += ev;
-      }
-      M[g * kMaxSrc + j] = m;
-    }
-  }
-
-  // --- Eqs. (2)-(6) -----------------------------------------------------------
-  float w[kMaxSrc];
-  uint32_t S;
-  int v;
-  const uint8_t vb = a.vbest[pi];
-  joint_view_selection(a, M, valid, a.sel[pi], vb == 255 ? -1 : (int)vb, w, &S, &v);
-  float sw = 0.f;
-  uint32_t wm = 0;
-  for (int j = 0; j < a.N; j++) {
-    sw += w[j];
-    wm |= (w[j] > 0.f ? 1u : 0u) << j;
-  }
-  const float inv_sw = 1.f / sw;
-
-  // --- Eq. (7): unified cost; the own plane competes and wins ties ----------
-  float4 best = a.plane[pi];
-  const Hyp own = make_hyp(a.Kinv, best, ray);
-  float bm = weighted_cost(a, own, fx, fy, rw, w, inv_sw, npairs);
-  int choice = 8;
-#pragma unroll 1
-  for (int g = 0; g < kRegions; g++) {
-    if (!(valid >> g & 1u)) continue;
-    float acc = 0.f;
-    for (int j = 0; j < a.N; j++)
-      if (w[j] > 0.f) acc = fmaf(w[j], M[g * kMaxSrc + j], acc);
-    acc *= inv_sw;
-    if (acc < bm) { bm = acc; best = hpl[g]; choice = g; }
-  }
-
-  // --- Sec. 3.3: refinement, same weights --------------------------------------
-  float4 cand[6];
-  const int nc = refine_candidates(a, x, y, best, ray, cand);
-  int bc = -1;
-  float bcm = 0.f;
-#pragma unroll 1
-  for (int c = 0; c < nc; c++) {
-    const Hyp h = make_hyp(a.Kinv, cand[c], ray);
-    const float m = weighted_cost(a, h, fx, fy, rw, w, inv_sw, npairs);
-    if (bc < 0 || m < bcm) { bc = c; bcm = m; }
-  }
-  if (bc >= 0 && bcm < bm) { bm = bcm; best = cand[bc]; choice = 9 + bc; }
-
-  a.plane[pi] = best;
-  a.cost[pi] = bm;
-  a.sel[pi] = S;
-  a.vbest[pi] = v < 0 ? (uint8_t)255 : (uint8_t)v;
-  a.wmask[pi] = wm;
-  a.choice[pi] = (uint8_t)choice;
-}
-
-// 16 x 16 pixel tile per block: 16 rows of 8 same-coloured pixels; a warp
-// covers 4 rows (a 16 x 4 footprint).
-constexpr int kTile = 16;
-constexpr int kPhaseThreads = 128;
-
-__global__ void __launch_bounds__(kPhaseThreads) phase_kernel(const __grid_constant__ PhaseArgs a) {
-  const int tid = threadIdx.x;
-  const int y = blockIdx.y * kTile + (tid >> 3);
-  const int x = blockIdx.x * kTile + 2 * (tid & 7) + ((y + a.color) & 1);
-  int npairs = 0;
-  if (x < a.W && y < a.H) update_pixel(a, x, y, &npairs);
-  const int tot = __reduce_add_sync(0xffffffffu, npairs);
-  if ((tid & 31) == 0 && tot) atomicAdd(a.pairs, (unsigned long long)tot);
-}
-
-// Random initialisation: one thread per pixel over the whole image.
-__global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ PhaseArgs a) {
-  const int x = blockIdx.x * 16 + (threadIdx.x & 15), y = blockIdx.y * 16 + (threadIdx.x >> 4);
-  int npairs = 0;
-  if (x < a.W && y < a.H) {
-    const size_t pi = (size_t)y * a.W + x;
-    const float fx = (float)x, fy = (float)y;
-    const float3 ray = ref_ray(a.Kinv, fx, fy);
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)pi, 0u, 0u, 0u), a.key0, a.key1);
-    const float3 n = face_camera(normal_from_uniforms(u01(r.y), u01(r.z)), ray);
-    const float D = a.dmin + (a.dmax - a.dmin) * u01(r.x);
-    const float4 pl = make_float4(n.x, n.y, n.z, D);
-    const Hyp h = make_hyp(a.Kinv, pl, ray);
-    RefWin rw;
-    load_ref_window(a, x, y, rw);
-    float m[kMaxSrc];
-    for (int j = 0; j < a.N; j++) {
-      int ev = 0;
-      m[j] = ncc_cost(a.v[j], h, fx, fy, rw, &ev);
-      npairs += ev;
-    }
-    // mean of the k smallest per-view costs (ties: lower view index)
-    const int k = a.k < a.N ? a.k : a.N;
-    uint32_t used = 0;
-    float acc = 0.f;
-    for (int r2 = 0; r2 < k; r2++) {
-      int bj = -1;
-      for (int j = 0; j < a.N; j++)
-        if (!(used >> j & 1u) && (bj < 0 || m[j] < m[bj])) bj = j;
-      used |= 1u << bj;
-      acc += m[bj];
-    }
-    a.plane[pi] = pl;
-    a.cost[pi] = acc / (float)k;
-    a.sel[pi] = 0;
-    a.vbest[pi] = 255;
-    a.wmask[pi] = 0;
-    a.choice[pi] = 8;
-  }
-  const int tot = __reduce_add_sync(0xffffffffu, npairs);
-  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(a.pairs, (unsigned long long)tot);
-}
-
 // depth / normal split of the plane array
 __global__ void split_maps_kernel(const float4* __restrict__ plane, size_t n, float* depth, float* normal3) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -354,7 +27,6 @@ __global__ void split_maps_kernel(const float4* __restrict__ plane, size_t n, fl
     if (normal3) { normal3[3 * i] = p.x; normal3[3 * i + 1] = p.y; normal3[3 * i + 2] = p.z; }
   }
 }
-
 }  // namespace amh
 
 // ===========================================================================
@@ -503,6 +175,8 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   if (!inv3(cr.K, Kri)) { delete c; return fail(nullptr, AMH_EINVAL, "reference K singular"); }
   const size_t np = (size_t)c->W * c->H;
   const cudaMemcpyKind kind = images_mem == AMH_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const bool half = (p->flags & AMH_FLAG_IMAGES_F16) != 0;
+  const size_t es = half ? 2 : 1;   // bytes per image element
 
   auto bail = [&](int code) {
     g_create_err = c->err;
@@ -520,16 +194,16 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     }                                                                                           \
   } while (0)
 
-  CTRY(cudaMalloc(&c->d_ref, np));
-  CTRY(cudaMemcpyAsync(c->d_ref, images[ref], np, kind, c->stream));
+  CTRY(cudaMalloc(&c->d_ref, np * es));
+  CTRY(cudaMemcpyAsync(c->d_ref, images[ref], np * es, kind, c->stream));
   CTRY(cudaMalloc(&c->d_plane, np * sizeof(float4)));
   CTRY(cudaMalloc(&c->d_cost, np * sizeof(float)));
   CTRY(cudaMalloc(&c->d_sel, np * sizeof(uint32_t)));
   CTRY(cudaMalloc(&c->d_vbest, np));
   CTRY(cudaMalloc(&c->d_wmask, np * sizeof(uint32_t)));
   CTRY(cudaMalloc(&c->d_choice, np));
-  CTRY(cudaMalloc(&c->d_pairs, sizeof(unsigned long long)));
-  CTRY(cudaMemsetAsync(c->d_pairs, 0, sizeof(unsigned long long), c->stream));
+  CTRY(cudaMalloc(&c->d_pairs, kPairCounters * sizeof(unsigned long long)));
+  CTRY(cudaMemsetAsync(c->d_pairs, 0, kPairCounters * sizeof(unsigned long long), c->stream));
 
   PhaseArgs& a = c->args;
   std::memset(&a, 0, sizeof a);
@@ -545,6 +219,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   a.wI = (float)(1.0 / (2.0 * (double)p->sigma_I * p->sigma_I));
   a.wX = (float)(1.0 / (2.0 * (double)p->sigma_x * p->sigma_x));
   a.squared = (p->flags & AMH_FLAG_BILATERAL_SQUARED) ? 1 : 0;
+  a.img_half = half ? 1 : 0;
   a.dmin = p->depth_min;
   a.dmax = p->depth_max;
   a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
@@ -582,10 +257,12 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     for (int i = 0; i < 3; i++) V.b[i] = (float)b[i];
     V.xmax = (float)cj.width;
     V.ymax = (float)cj.height;
-    // texture array
-    cudaChannelFormatDesc fd = cudaCreateChannelDesc<uint8_t>();
+    // the view as a texture: point sampling, clamp to edge; uint8 read as
+    // value / 255, FP16 read as the value
+    cudaChannelFormatDesc fd = half ? cudaCreateChannelDescHalf() : cudaCreateChannelDesc<uint8_t>();
     CTRY(cudaMallocArray(&c->arr[j], &fd, cj.width, cj.height, cudaArrayTextureGather));
-    CTRY(cudaMemcpy2DToArrayAsync(c->arr[j], 0, 0, images[v], cj.width, cj.width, cj.height, kind, c->stream));
+    CTRY(cudaMemcpy2DToArrayAsync(c->arr[j], 0, 0, images[v], cj.width * es, cj.width * es, cj.height, kind,
+                                  c->stream));
     cudaResourceDesc rd;
     std::memset(&rd, 0, sizeof rd);
     rd.resType = cudaResourceTypeArray;
@@ -595,7 +272,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     td.addressMode[0] = cudaAddressModeClamp;
     td.addressMode[1] = cudaAddressModeClamp;
     td.filterMode = cudaFilterModePoint;
-    td.readMode = cudaReadModeNormalizedFloat;
+    td.readMode = half ? cudaReadModeElementType : cudaReadModeNormalizedFloat;
     td.normalizedCoords = 0;
     CTRY(cudaCreateTextureObject(&c->tex[j], &rd, &td, nullptr));
     V.tex = c->tex[j];
@@ -616,8 +293,7 @@ AMH_API int amh_init_random(amh_ctx* c) {
   if (!c) return AMH_EINVAL;
   c->t = 0;
   fill_step_args(c, 0);
-  dim3 grid((c->W + 15) / 16, (c->H + 15) / 16);
-  init_kernel<<<grid, 256, 0, c->stream>>>(c->args);
+  launch_init(c->args, c->stream);
   int rc = launch_check(c, "init");
   if (rc) return rc;
   c->initialized = true;
@@ -629,8 +305,7 @@ AMH_API int amh_step_phase(amh_ctx* c, int32_t color) {
   if (color != 0 && color != 1) return fail(c, AMH_EINVAL, "color must be 0 or 1");
   if (!c->initialized) return fail(c, AMH_ESTATE, "state not initialised (amh_init_random or amh_set_state)");
   fill_step_args(c, color);
-  dim3 grid((c->W + kTile - 1) / kTile, (c->H + kTile - 1) / kTile);
-  phase_kernel<<<grid, kPhaseThreads, 0, c->stream>>>(c->args);
+  launch_phase(c->args, c->stream);
   int rc = launch_check(c, "phase");
   if (rc) return rc;
   if (color == 1) c->t++;
@@ -734,11 +409,13 @@ AMH_API int amh_get_info(const amh_ctx* c, int32_t* w, int32_t* h, int32_t* n, i
 
 AMH_API int amh_pair_count(amh_ctx* c, uint64_t* count, int32_t reset) {
   if (!c) return AMH_EINVAL;
-  unsigned long long v = 0;
-  CUDA_TRY(c, cudaMemcpyAsync(&v, c->d_pairs, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long v[kPairCounters];
+  CUDA_TRY(c, cudaMemcpyAsync(v, c->d_pairs, sizeof v, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  if (count) *count = v;
-  if (reset) CUDA_TRY(c, cudaMemsetAsync(c->d_pairs, 0, sizeof(unsigned long long), c->stream));
+  unsigned long long tot = 0;
+  for (int i = 0; i < kPairCounters; i++) tot += v[i];
+  if (count) *count = tot;
+  if (reset) CUDA_TRY(c, cudaMemsetAsync(c->d_pairs, 0, sizeof v, c->stream));
   return AMH_OK;
 }
 

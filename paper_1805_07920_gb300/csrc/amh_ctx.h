@@ -13,16 +13,16 @@ struct amh_ctx {
   int W = 0, H = 0, N = 0, ref = 0;
   int src[AMH_MAX_SRC];
   cudaStream_t stream = nullptr;
-  cudaArray_t arr[AMH_MAX_SRC] = {};
+  cudaArray_t arr[AMH_MAX_SRC] = {};      // source views, uint8 texture arrays
   cudaTextureObject_t tex[AMH_MAX_SRC] = {};
-  uint8_t* d_ref = nullptr;
+  void* d_ref = nullptr;                  // reference image (uint8 or FP16)
   float4* d_plane = nullptr;
   float* d_cost = nullptr;
   uint32_t* d_sel = nullptr;
   uint8_t* d_vbest = nullptr;
   uint32_t* d_wmask = nullptr;
   uint8_t* d_choice = nullptr;
-  unsigned long long* d_pairs = nullptr;
+  unsigned long long* d_pairs = nullptr;  // amh::kPairCounters striped counters
   amh::PhaseArgs args;
   int t = 0;
   bool initialized = false;

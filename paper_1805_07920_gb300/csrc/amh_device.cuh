@@ -1,11 +1,10 @@
 // amh_device.cuh -- device building blocks of the checkerboard update:
-// Philox4x32-10, random planes, the plane-induced homography, the warped
-// bilateral weighted NCC over the skipping window (Eq. 8) and the
-// multi-hypothesis joint view selection (Eqs. 2-7).
+// Philox4x32-10, random planes, the plane-induced homography and the kernel
+// argument block.
 //
-// Written for sm_103a.  FP32 arithmetic throughout; the source images are
-// uint8 textures read with tex2Dgather (four texels per fetch, clamp-to-edge
-// addressing done by the texture unit) and interpolated in FP32.
+// Written for sm_103a.  FP32 arithmetic throughout; every source view is a
+// uint8 texture read with tex2Dgather (four texels per fetch, clamp-to-edge
+// addressing in the texture unit) and interpolated in FP32.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,18 +18,22 @@ constexpr int kWinStride = 2;            // ... every other row and column
 constexpr int kWinN = 2 * kWinR / kWinStride + 1;   // 6 samples per axis
 constexpr int kWinS = kWinN * kWinN;                // 36 samples
 constexpr float kWorst = 2.0f;           // cost of an invalid (hypothesis, view)
+constexpr int kMaxRefine = 6;
+constexpr int kPairCounters = 64;        // striped evaluation counters
 
 // One source view.  A and b give the homography of a plane (n, d) as
 // H = A - b c^T with c = K_ref^-T n / d (Sec. 2: planes in scene space), where
 // A = K_j R_jr K_ref^-1 and b = K_j t_jr; rows 0 and 1 already hold row 2
-// added once, so that H maps reference pixels to source coordinates + (1, 1),
-// the coordinate tex2Dgather needs to fetch texels (floor(x), floor(x) + 1).
+// added once, so H maps reference pixels to source coordinates + (1, 1): with
+// integer part f of such a coordinate, tex2Dgather at f fetches the texels
+// (f - 1, f) = (floor(x), floor(x) + 1).
 struct ViewConst {
   float A[9];
   float b[3];
-  float xmax, ymax;          // width, height (valid shifted centre: [1, W] x [1, H])
-  cudaTextureObject_t tex;   // uint8, point sampling, clamp, normalised float
+  float xmax, ymax;          // width, height: valid shifted centres in [1, W] x [1, H]
+  cudaTextureObject_t tex;   // point sampling, clamp; uint8 read as value / 255, or FP16
 };
+static_assert(sizeof(ViewConst) == 64, "ViewConst is 64 bytes");
 
 struct PhaseArgs {
   int W, H, N, color, t;
@@ -41,16 +44,17 @@ struct PhaseArgs {
   float inv2beta2;           // 1 / (2 beta^2), Eq. (3)
   float wI, wX;              // 1 / (2 sigma_I^2), 1 / (2 sigma_x^2), Eq. (8)
   int squared;               // bilateral weight on squared differences
+  int img_half;              // images are FP16 (else uint8)
   float dmin, dmax;
   uint32_t key0, key1;       // Philox key (seed)
-  const uint8_t* ref;        // reference image, W x H
+  const void* ref;           // reference image, W x H (uint8 or FP16)
   float4* plane;
   float* cost;
   uint32_t* sel;
   uint8_t* vbest;
   uint32_t* wmask;
   uint8_t* choice;
-  unsigned long long* pairs; // (hypothesis, view) evaluations
+  unsigned long long* pairs; // kPairCounters striped (hypothesis, view) evaluation counters
   ViewConst v[kMaxSrc];
 };
 
@@ -102,138 +106,17 @@ __device__ __forceinline__ float3 normal_from_uniforms(float u1, float u2) {
   return make_float3(r * c, r * s, z);
 }
 
-// A hypothesis in the form the cost needs: c = K_ref^-T n / d (Sec. 2), with
-// d = -D (n . ray) the plane offset; valid when the plane faces the pixel.
-struct Hyp {
-  float4 pl;    // (n, D at this pixel)
-  float3 c;
-  bool ok;
-};
-__device__ __forceinline__ Hyp make_hyp(const float* Ki, float4 pl, float3 ray) {
-  Hyp h;
-  h.pl = pl;
-  float3 n = make_float3(pl.x, pl.y, pl.z);
-  float d = -pl.w * dot3(n, ray);
-  h.ok = (pl.w > 0.f) && (d > 0.f) && isfinite(d);
-  float id = h.ok ? 1.f / d : 0.f;
-  h.c = make_float3((Ki[0] * n.x + Ki[3] * n.y + Ki[6] * n.z) * id,
-                    (Ki[1] * n.x + Ki[4] * n.y + Ki[7] * n.z) * id,
-                    (Ki[2] * n.x + Ki[5] * n.y + Ki[8] * n.z) * id);
-  return h;
-}
-
-// ---------------------------------------------------------------------------
-// Reference window of one pixel (Sec. 3.3): 36 samples at offsets
-// {-5,-3,-1,1,3,5}^2 clamped to the image, bilateral weights
-// w = exp(-|I - I_c| / (2 sigma_I^2) - |dx| / (2 sigma_x^2)), and the
-// weighted-centred reference values so that cov(r, s) = sum w r^ s / sum w.
-// ---------------------------------------------------------------------------
-struct RefWin {
-  float w[kWinS];
-  float wr[kWinS];    // w * (r - E_w r)
-  float inv_sw;       // 1 / sum w
-  float sum_wr;       // sum w (r - E_w r), ~0
-  float var_r;        // weighted variance of r (0..255 units)
-};
-
-__device__ __forceinline__ void load_ref_window(const PhaseArgs& a, int x, int y, RefWin& rw) {
-  const uint8_t* I = a.ref;
-  const float Ic = (float)__ldg(&I[(size_t)y * a.W + x]);
-  float rv[kWinS];
-  float sw = 0.f, s1 = 0.f;
-#pragma unroll
-  for (int k = 0; k < kWinS; k++) {
-    const int du = -kWinR + kWinStride * (k % kWinN), dv = -kWinR + kWinStride * (k / kWinN);
-    const int xr = min(max(x + du, 0), a.W - 1), yr = min(max(y + dv, 0), a.H - 1);
-    const float r = (float)__ldg(&I[(size_t)yr * a.W + xr]) - Ic;   // exact
-    const float dist = sqrtf((float)(du * du + dv * dv));
-    float dI = fabsf(r), dx = dist;
-    if (a.squared) { dI = r * r; dx = (float)(du * du + dv * dv); }
-    const float w = expf(-dI * a.wI - dx * a.wX);
-    rv[k] = r;
-    rw.w[k] = w;
-    sw += w;
-    s1 = fmaf(w, r, s1);
-  }
-  const float inv = 1.f / sw;
-  const float mr = s1 * inv;
-  float s2 = 0.f, swr = 0.f;
-#pragma unroll
-  for (int k = 0; k < kWinS; k++) {
-    const float rc = rv[k] - mr;
-    const float wr = rw.w[k] * rc;
-    rw.wr[k] = wr;
-    swr += wr;
-    s2 = fmaf(wr, rc, s2);
-  }
-  rw.inv_sw = inv;
-  rw.sum_wr = swr;
-  rw.var_r = s2 * inv - (swr * inv) * (swr * inv);
-}
-
-// ---------------------------------------------------------------------------
-// Eq. (8): cost of one hypothesis against one source view.  Returns 2 when
-// the plane is invalid, lies behind view j over the window, or projects the
-// centre outside view j, or when a patch has no variance; else clamps to
-// [0, 2].  *evaluated is set when the 36 samples were taken.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float ncc_cost(const ViewConst& V, const Hyp& h, float x, float y,
-                                          const RefWin& rw, int* evaluated) {
-  if (!h.ok) return kWorst;
-  // H = A - b c^T
-  const float H0 = fmaf(-V.b[0], h.c.x, V.A[0]), H1 = fmaf(-V.b[0], h.c.y, V.A[1]),
-              H2 = fmaf(-V.b[0], h.c.z, V.A[2]);
-  const float H3 = fmaf(-V.b[1], h.c.x, V.A[3]), H4 = fmaf(-V.b[1], h.c.y, V.A[4]),
-              H5 = fmaf(-V.b[1], h.c.z, V.A[5]);
-  const float H6 = fmaf(-V.b[2], h.c.x, V.A[6]), H7 = fmaf(-V.b[2], h.c.y, V.A[7]),
-              H8 = fmaf(-V.b[2], h.c.z, V.A[8]);
-  // homogeneous depth is affine over the window: check its minimum corner
-  const float pz = fmaf(H6, x, fmaf(H7, y, H8));
-  const float zmin = pz - (float)kWinR * (fabsf(H6) + fabsf(H7));
-  if (!(zmin > 0.f)) return kWorst;
-  const float px = fmaf(H0, x, fmaf(H1, y, H2)), py = fmaf(H3, x, fmaf(H4, y, H5));
-  const float iz = 1.f / pz;
-  const float cx = px * iz, cy = py * iz;
-  if (!(cx >= 1.f && cx <= V.xmax && cy >= 1.f && cy <= V.ymax)) return kWorst;
-  *evaluated = 1;
-  // window corner (-R, -R) and the steps between samples
-  const float sx0 = px - (float)kWinR * (H0 + H1), sy0 = py - (float)kWinR * (H3 + H4),
-              sz0 = pz - (float)kWinR * (H6 + H7);
-  const float cxs = (float)kWinStride * H0, cys = (float)kWinStride * H3, czs = (float)kWinStride * H6;
-  const float rxs = (float)kWinStride * H1, rys = (float)kWinStride * H4, rzs = (float)kWinStride * H7;
-  float s0 = 0.f, m1 = 0.f, m2 = 0.f, mrs = 0.f;
-#pragma unroll
-  for (int a = 0; a < kWinN; a++) {
-    const float ax = fmaf((float)a, rxs, sx0), ay = fmaf((float)a, rys, sy0), az = fmaf((float)a, rzs, sz0);
-#pragma unroll
-    for (int b = 0; b < kWinN; b++) {
-      const int k = a * kWinN + b;
-      const float qx = fmaf((float)b, cxs, ax), qy = fmaf((float)b, cys, ay), qz = fmaf((float)b, czs, az);
-      const float iq = rcp_approx(qz);
-      const float gx = qx * iq, gy = qy * iq;
-      const float fx0 = floorf(gx), fy0 = floorf(gy);
-      const float fx = gx - fx0, fy = gy - fy0;
-      // texels: w (x0, y0), z (x0+1, y0), x (x0, y0+1), y (x0+1, y0+1)
-      const float4 g = tex2Dgather<float4>(V.tex, fx0, fy0, 0);
-      const float top = fmaf(fx, g.z - g.w, g.w);
-      const float bot = fmaf(fx, g.y - g.x, g.x);
-      const float s = fmaf(fy, bot - top, top);
-      if (k == 0) s0 = s;
-      const float sc = s - s0;
-      const float ws = rw.w[k] * sc;
-      m1 += ws;
-      m2 = fmaf(ws, sc, m2);
-      mrs = fmaf(rw.wr[k], sc, mrs);
-    }
-  }
-  const float es = m1 * rw.inv_sw;
-  const float var_s = fmaf(m2, rw.inv_sw, -es * es);
-  const float cov = fmaf(mrs, rw.inv_sw, -(rw.sum_wr * rw.inv_sw) * es);
-  // variances in (0..255)^2 units: the texture returns intensities / 255
-  const float vv = rw.var_r * var_s * (255.f * 255.f);
-  if (!(vv >= 1e-10f)) return kWorst;
-  float m = 1.f - cov * (255.f * rsqrtf(vv));
-  return fminf(fmaxf(m, 0.f), 2.f);
+// The cost needs c = K_ref^-T n / d (Sec. 2) with d = -D (n . ray) the plane
+// offset; the plane is usable when it faces the pixel (d > 0) at D > 0.
+__device__ __forceinline__ bool plane_c(const float* Ki, float4 pl, float3 ray, float3* c) {
+  const float3 n = make_float3(pl.x, pl.y, pl.z);
+  const float d = -pl.w * dot3(n, ray);
+  const bool ok = (pl.w > 0.f) && (d > 0.f) && isfinite(d);
+  const float id = ok ? 1.f / d : 0.f;
+  *c = make_float3((Ki[0] * n.x + Ki[3] * n.y + Ki[6] * n.z) * id,
+                   (Ki[1] * n.x + Ki[4] * n.y + Ki[7] * n.z) * id,
+                   (Ki[2] * n.x + Ki[5] * n.y + Ki[8] * n.z) * id);
+  return ok;
 }
 
 }  // namespace amh

@@ -1,0 +1,79 @@
+// amh_kernels.cu -- kernels of the single-reference context: random
+// initialisation and one colour phase over a 16 x 16 tile per block (the
+// update itself is in amh_update.cuh).
+#include <cuda_runtime.h>
+
+#include "amh_device.cuh"
+#include "amh_kernels.h"
+#include "amh_update.cuh"
+
+namespace amh {
+namespace {
+using namespace upd;
+
+constexpr int kTile = 16;
+constexpr int kThreads = 128;
+constexpr int kPhaseBlocksPerSM = 3;          // 168 registers per thread
+
+__device__ __forceinline__ void count_pairs(const PhaseArgs& a, int npairs) {
+  const int tot = __reduce_add_sync(0xffffffffu, npairs);
+  if ((threadIdx.x & 31) == 0 && tot)
+    atomicAdd(&a.pairs[(blockIdx.x * 4 + (threadIdx.x >> 5) + blockIdx.y * 7) % kPairCounters],
+              (unsigned long long)tot);
+}
+
+template <bool kHalf>
+__global__ void __launch_bounds__(kThreads, kPhaseBlocksPerSM) phase_kernel(const __grid_constant__ PhaseArgs a) {
+  PixelArrays sm;
+  const int tid = threadIdx.x;
+  const int y = blockIdx.y * kTile + (tid >> 3);
+  const int x = blockIdx.x * kTile + 2 * (tid & 7) + ((y + a.color) & 1);
+  int npairs = 0;
+  if (x < a.W && y < a.H) update_pixel<kHalf>(a, sm, x, y, &npairs);
+  count_pairs(a, npairs);
+}
+
+// Random initialisation: one thread per pixel over the whole image.
+template <bool kHalf>
+__global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ PhaseArgs a) {
+  PixelArrays sm;
+  const int x = blockIdx.x * kTile + (threadIdx.x & 15), y = blockIdx.y * 8 + (threadIdx.x >> 4);
+  int npairs = 0;
+  if (x < a.W && y < a.H) init_pixel<kHalf>(a, sm, x, y, &npairs);
+  count_pairs(a, npairs);
+}
+
+
+}  // namespace
+
+// Both kernels use no shared memory: ask for the largest L1 (texture cache).
+template <typename K>
+void prefer_l1(K kernel) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+}
+
+template <bool kHalf>
+int launch_init_t(const PhaseArgs& a, cudaStream_t s) {
+  static bool once = (prefer_l1(init_kernel<kHalf>), true);
+  (void)once;
+  dim3 grid((a.W + kTile - 1) / kTile, (a.H + 7) / 8);
+  init_kernel<kHalf><<<grid, kThreads, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+int launch_init(const PhaseArgs& a, cudaStream_t s) {
+  return a.img_half ? launch_init_t<true>(a, s) : launch_init_t<false>(a, s);
+}
+
+template <bool kHalf>
+int launch_phase_t(const PhaseArgs& a, cudaStream_t s) {
+  static bool once = (prefer_l1(phase_kernel<kHalf>), true);
+  (void)once;
+  dim3 grid((a.W + kTile - 1) / kTile, (a.H + kTile - 1) / kTile);
+  phase_kernel<kHalf><<<grid, kThreads, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+int launch_phase(const PhaseArgs& a, cudaStream_t s) {
+  return a.img_half ? launch_phase_t<true>(a, s) : launch_phase_t<false>(a, s);
+}
+
+}  // namespace amh

@@ -1,0 +1,472 @@
+// amh_update.cuh -- one pixel's checkerboard update and its parts, shared by
+// the single-reference kernels (amh_kernels.cu) and the batched persistent
+// kernels (amh_batch.cu).  The argument block is a template parameter: any
+// struct with the fields of PhaseArgs (sizes, parameters, state pointers and
+// an indexable view table v) works.
+//
+// Work mapping: one thread per reference pixel; a warp updates 32 pixels of
+// one colour of a compact tile, so the lanes of every texture gather sample
+// neighbouring windows of the same source view.  Every (hypothesis, view)
+// loop runs with a warp-uniform view index (uniform texture handle).  Each
+// thread keeps its 36 bilateral weights in registers and its cost matrix and
+// view weights in local memory (L1); no shared memory is needed, so the whole
+// L1 serves the texture gathers.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "amh_device.cuh"
+
+namespace amh {
+namespace upd {
+
+
+// Sec. 3.1, Fig. 2(d): candidate c of the 72 in scan order.  Regions 0..3
+// (near up/down/left/right) hold 7 candidates: the axis pixel at distance 1
+// and the pairs at lateral offset -+a, distance a + 1 (a = 1..3); regions
+// 4..7 (far) hold the axis pixels at distances 3, 5, ..., 23.
+__host__ __device__ constexpr int acp_region(int c) { return c < 28 ? c / 7 : 4 + (c - 28) / 11; }
+__host__ __device__ constexpr int acp_index(int c) { return c < 28 ? c % 7 : (c - 28) % 11; }
+__host__ __device__ constexpr int acp_start(int g) { return g < 4 ? 7 * g : 28 + 11 * (g - 4); }
+__host__ __device__ constexpr int acp_depth(int c) {
+  return acp_region(c) < 4 ? (acp_index(c) + 1) / 2 + 1 : 3 + 2 * acp_index(c);
+}
+__host__ __device__ constexpr int acp_lateral(int c) {
+  return acp_region(c) < 4 && acp_index(c) > 0 ? ((acp_index(c) & 1) ? -1 : 1) * ((acp_index(c) + 1) / 2) : 0;
+}
+__host__ __device__ constexpr int acp_dx(int c) {
+  return (acp_region(c) & 3) == 2 ? -acp_depth(c) : (acp_region(c) & 3) == 3 ? acp_depth(c) : acp_lateral(c);
+}
+__host__ __device__ constexpr int acp_dy(int c) {
+  return (acp_region(c) & 3) == 0 ? -acp_depth(c) : (acp_region(c) & 3) == 1 ? acp_depth(c) : acp_lateral(c);
+}
+static_assert(acp_dx(0) == 0 && acp_dy(0) == -1, "near up starts at (0, -1)");
+static_assert(acp_dx(1) == -1 && acp_dy(1) == -2 && acp_dx(2) == 1 && acp_dy(2) == -2, "V arms");
+static_assert(acp_dx(6) == 3 && acp_dy(6) == -4, "near up ends at (3, -4)");
+static_assert(acp_dx(15) == -2 && acp_dy(15) == -1, "near left (-2, -1)");
+static_assert(acp_dx(28) == 0 && acp_dy(28) == -3 && acp_dy(38) == -23, "far up strip 3..23");
+static_assert(acp_dx(71) == 23 && acp_dy(71) == 0, "far right ends at (23, 0)");
+
+// Reference window of one pixel (Sec. 3.3): 36 samples at offsets
+// {-5,-3,-1,1,3,5}^2 clamped to the image; w = exp(-|I - I_c| / (2 sigma_I^2)
+// - |dx| / (2 sigma_x^2)); the values centred on their weighted mean so that
+// cov(r, s) = sum w r^ s / sum w.
+struct RefWin {
+  float w[kWinS];
+  float wr[kWinS];
+  float inv_sw, sum_wr, var_r;
+};
+
+// intensity of reference pixel i (uint8 or FP16 images)
+template <bool kHalf, class A>
+__device__ __forceinline__ float ref_at(const A& a, size_t i) {
+  if (kHalf) return __half2float(__ldg(reinterpret_cast<const __half*>(a.ref) + i));
+  return (float)__ldg(reinterpret_cast<const uint8_t*>(a.ref) + i);
+}
+// Source textures return intensity / 255 for uint8 images (normalised read)
+// and the intensity itself for FP16 images.
+template <bool kHalf>
+__host__ __device__ constexpr float tex_scale() { return kHalf ? 1.f : 255.f; }
+
+template <bool kHalf, class A>
+__device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin& rw) {
+  const float Ic = ref_at<kHalf, A>(a, (size_t)y * a.W + x);
+  float rv[kWinS];
+  float sw = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < kWinS; k++) {
+    const int du = -kWinR + kWinStride * (k % kWinN), dv = -kWinR + kWinStride * (k / kWinN);
+    const int xr = min(max(x + du, 0), a.W - 1), yr = min(max(y + dv, 0), a.H - 1);
+    const float r = ref_at<kHalf, A>(a, (size_t)yr * a.W + xr) - Ic;   // exact
+    float dI = fabsf(r), dx = sqrtf((float)(du * du + dv * dv));
+    if (a.squared) { dI = r * r; dx = (float)(du * du + dv * dv); }
+    const float w = expf(-dI * a.wI - dx * a.wX);
+    rv[k] = r;
+    rw.w[k] = w;
+    sw += w;
+    s1 = fmaf(w, r, s1);
+  }
+  const float inv = 1.f / sw;
+  const float mr = s1 * inv;
+  float s2 = 0.f, swr = 0.f;
+#pragma unroll
+  for (int k = 0; k < kWinS; k++) {
+    const float rc = rv[k] - mr;
+    const float wr = rw.w[k] * rc;
+    rw.wr[k] = wr;
+    swr += wr;
+    s2 = fmaf(wr, rc, s2);
+  }
+  rw.inv_sw = inv;
+  rw.sum_wr = swr;
+  rw.var_r = s2 * inv - (swr * inv) * (swr * inv);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (8): cost of the plane c = K^-T n / d against view V at pixel (x, y).
+// 2 when the plane is unusable (ok false), lies behind view j over the window
+// (homogeneous depth <= 0 at a window corner; it is affine over the window),
+// projects the centre outside view j, or when a patch has no variance;
+// otherwise clamped to [0, 2].  Window samples outside the view are clamped to
+// its edge by the texture unit.
+// ---------------------------------------------------------------------------
+template <bool kHalf>
+__device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok, float x, float y,
+                                          const RefWin& rw, int* evaluated) {
+  if (!ok) return kWorst;
+  const float H0 = fmaf(-V.b[0], c.x, V.A[0]), H1 = fmaf(-V.b[0], c.y, V.A[1]), H2 = fmaf(-V.b[0], c.z, V.A[2]);
+  const float H3 = fmaf(-V.b[1], c.x, V.A[3]), H4 = fmaf(-V.b[1], c.y, V.A[4]), H5 = fmaf(-V.b[1], c.z, V.A[5]);
+  const float H6 = fmaf(-V.b[2], c.x, V.A[6]), H7 = fmaf(-V.b[2], c.y, V.A[7]), H8 = fmaf(-V.b[2], c.z, V.A[8]);
+  const float pz = fmaf(H6, x, fmaf(H7, y, H8));
+  const float zmin = pz - (float)kWinR * (fabsf(H6) + fabsf(H7));
+  if (!(zmin > 0.f)) return kWorst;
+  const float px = fmaf(H0, x, fmaf(H1, y, H2)), py = fmaf(H3, x, fmaf(H4, y, H5));
+  const float iz = 1.f / pz;
+  const float cx = px * iz, cy = py * iz;
+  if (!(cx >= 1.f && cx <= V.xmax && cy >= 1.f && cy <= V.ymax)) return kWorst;
+  *evaluated += 1;
+  const float R = (float)kWinR, St = (float)kWinStride;
+  const float sx0 = fmaf(-R, H0 + H1, px), sy0 = fmaf(-R, H3 + H4, py), sz0 = fmaf(-R, H6 + H7, pz);
+  const float cxs = St * H0, cys = St * H3, czs = St * H6;
+  const float rxs = St * H1, rys = St * H4, rzs = St * H7;
+  float s0 = 0.f, m1 = 0.f, m2 = 0.f, mrs = 0.f;
+#pragma unroll
+  for (int ra = 0; ra < kWinN; ra++) {
+    const float bx = fmaf((float)ra, rxs, sx0), by = fmaf((float)ra, rys, sy0), bz = fmaf((float)ra, rzs, sz0);
+#pragma unroll
+    for (int cb = 0; cb < kWinN; cb++) {
+      const int k = ra * kWinN + cb;
+      const float qx = fmaf((float)cb, cxs, bx), qy = fmaf((float)cb, cys, by), qz = fmaf((float)cb, czs, bz);
+      const float iq = rcp_approx(qz);
+      const float gx = qx * iq, gy = qy * iq;
+      const float fx0 = floorf(gx), fy0 = floorf(gy);
+      const float fx = gx - fx0, fy = gy - fy0;
+      // texels: w (x0, y0), z (x0+1, y0), x (x0, y0+1), y (x0+1, y0+1)
+      const float4 g = tex2Dgather<float4>(V.tex, fx0, fy0, 0);
+      const float top = fmaf(fx, g.z - g.w, g.w);
+      const float bot = fmaf(fx, g.y - g.x, g.x);
+      const float s = fmaf(fy, bot - top, top);
+      // moments about the first sample: exact zero variance for constant
+      // patches in FP32
+      if (k == 0) s0 = s;
+      const float sc = s - s0;
+      const float ws = rw.w[k] * sc;
+      m1 += ws;
+      m2 = fmaf(ws, sc, m2);
+      mrs = fmaf(rw.wr[k], sc, mrs);
+    }
+  }
+  const float es = m1 * rw.inv_sw;
+  const float var_s = fmaf(m2, rw.inv_sw, -es * es);
+  const float cov = fmaf(mrs, rw.inv_sw, -(rw.sum_wr * rw.inv_sw) * es);
+  // variances in squared intensity units (the threshold is 1e-10 there)
+  constexpr float S = tex_scale<kHalf>();
+  const float vv = rw.var_r * var_s * (S * S);
+  if (!(vv >= 1e-10f)) return kWorst;
+  return fminf(fmaxf(1.f - cov * (S * rsqrtf(vv)), 0.f), 2.f);
+}
+
+// Refinement candidate idx (Sec. 3.3): rho_t = 2^-(t+1); 0: depth and normal
+// perturbed (bisection); from t = 3 on also 1: (random D, n), 2: (D, random
+// n), 3: (random D, random n), 4: (perturbed D, n), 5: (D, perturbed n).
+// Draws (pixel, t, 0, 1) and (pixel, t, 1, 1).
+template <class A>
+__device__ __forceinline__ float4 refine_candidate(const A& a, int x, int y, float4 pl, float3 ray,
+                                                   int idx) {
+  const uint32_t pix = (uint32_t)(y * a.W + x);
+  const float rho = ldexpf(1.f, -(a.t + 1));
+  float Dp = pl.w;
+  float3 np = make_float3(pl.x, pl.y, pl.z);
+  if (idx == 0 || idx == 4 || idx == 5) {
+    const uint4 r0 = philox4x32_10(make_uint4(pix, (uint32_t)a.t, 0u, 1u), a.key0, a.key1);
+    Dp = pl.w * (1.f + rho * (2.f * u01(r0.x) - 1.f));
+    np = make_float3(pl.x + rho * (2.f * u01(r0.y) - 1.f), pl.y + rho * (2.f * u01(r0.z) - 1.f),
+                     pl.z + rho * (2.f * u01(r0.w) - 1.f));
+    const float inn = 1.f / sqrtf(dot3(np, np));
+    np = face_camera(make_float3(np.x * inn, np.y * inn, np.z * inn), ray);
+  }
+  float Dr = pl.w;
+  float3 nr = make_float3(pl.x, pl.y, pl.z);
+  if (idx >= 1 && idx <= 3) {
+    const uint4 r1 = philox4x32_10(make_uint4(pix, (uint32_t)a.t, 1u, 1u), a.key0, a.key1);
+    Dr = a.dmin + (a.dmax - a.dmin) * u01(r1.x);
+    nr = face_camera(normal_from_uniforms(u01(r1.y), u01(r1.z)), ray);
+  }
+  switch (idx) {
+    case 0: return make_float4(np.x, np.y, np.z, Dp);
+    case 1: return make_float4(pl.x, pl.y, pl.z, Dr);
+    case 2: return make_float4(nr.x, nr.y, nr.z, pl.w);
+    case 3: return make_float4(nr.x, nr.y, nr.z, Dr);
+    case 4: return make_float4(pl.x, pl.y, pl.z, Dp);
+    default: return make_float4(np.x, np.y, np.z, pl.w);
+  }
+}
+
+// Per-pixel working arrays of one thread (local memory, cached in L1): the
+// 8 x N cost matrix of Eq. (1), the N view weights and the 8 propagated planes
+// as c = K^-T n / d.  Shared memory stays unused so that L1 serves the texture
+// gathers.
+struct PixelArrays {
+  float M[kRegions * kMaxSrc];
+  float w[kMaxSrc];
+  float C[kRegions * 3];
+  __device__ float& m(int g, int j, int) { return M[g * kMaxSrc + j]; }
+  __device__ float& wt(int j) { return w[j]; }
+  __device__ float& cc(int g, int e) { return C[g * 3 + e]; }
+};
+
+// Eqs. (2)-(6): weights of the N views from the 8 x N matrix (rows of invalid
+// regions are left out of the counts and of the mean of Eq. (4)).
+template <class A>
+__device__ __forceinline__ void joint_view_selection(const A& a, PixelArrays& sm, uint32_t valid,
+                                                     uint32_t S_prev, int v_prev, uint32_t* S_out, int* v_out) {
+  const int N = a.N;
+  const int nvalid = __popc(valid);
+  const int k = a.k < N ? a.k : N;
+  uint32_t S = 0;
+  for (int j = 0; j < N; j++) {         // psi_mod of the good views into w
+    int ng = 0, nb = 0;
+    float psi = 0.f;
+#pragma unroll
+    for (int i = 0; i < kRegions; i++) {
+      if (!(valid >> i & 1u)) continue;
+      const float m = sm.m(i, j, N);
+      ng += m < a.tau;
+      nb += m > a.tau_up;
+      psi += expf(-m * m * a.inv2beta2);          // Eq. (3)
+    }
+    float pm = 0.f;
+    if (ng > a.n1 && nb < a.n2) {                  // good view
+      S |= 1u << j;
+      psi = psi / (float)nvalid;                   // Eq. (4)
+      pm = (j == v_prev) ? 2.f * psi : psi;        // Eqs. (5), (6)
+    }
+    sm.wt(j) = pm;
+  }
+  uint32_t kept = 0;
+  int v = -1;
+  for (int j = 0; j < N; j++) {
+    if (!(S >> j & 1u)) continue;
+    const float pj = sm.wt(j);
+    int rank = 0;
+    for (int q = 0; q < N; q++) {
+      const float pq = sm.wt(q);
+      rank += (S >> q & 1u) && (pq > pj || (pq == pj && q < j));
+    }
+    if (rank < k) kept |= 1u << j;                 // at most k views keep weight
+    if (rank == 0) v = j;
+  }
+  bool any = false;
+  for (int j = 0; j < N; j++) {
+    float wj;
+    if (S >> j & 1u) wj = (kept >> j & 1u) ? sm.wt(j) : 0.f;
+    else wj = (S_prev >> j & 1u) ? 0.2f : 0.f;   // selected at t - 1, not at t
+    sm.wt(j) = wj;
+    any = any || wj > 0.f;
+  }
+  if (!any) {  // no weight at all: the k views of smallest mean cost get 1
+    for (int j = 0; j < N; j++) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < kRegions; i++)
+        if (valid >> i & 1u) s += sm.m(i, j, N);
+      sm.wt(j) = nvalid ? s / (float)nvalid : 0.f;
+    }
+    uint32_t low = 0;
+    for (int j = 0; j < N; j++) {
+      const float cj = sm.wt(j);
+      int rank = 0;
+      for (int q = 0; q < N; q++) {
+        const float cq = sm.wt(q);
+        rank += cq < cj || (cq == cj && q < j);
+      }
+      if (rank < k) low |= 1u << j;
+    }
+    for (int j = 0; j < N; j++) sm.wt(j) = (low >> j & 1u) ? 1.f : 0.f;
+  }
+  *S_out = S;
+  *v_out = v;
+}
+
+
+// ---------------------------------------------------------------------------
+// one pixel's checkerboard update
+// ---------------------------------------------------------------------------
+template <bool kHalf, class A>
+__device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x, int y,
+                                             int* npairs) {
+  const int N = a.N;
+  const size_t pi = (size_t)y * a.W + x;
+  const float fx = (float)x, fy = (float)y;
+  const float3 ray = ref_ray(a.Kinv, fx, fy);
+
+  // --- Sec. 3.1: asymmetric checkerboard propagation ---------------------------
+  int pick[kRegions];
+#pragma unroll
+  for (int g = 0; g < kRegions; g++) {
+    int best = -1;
+    float bc = 0.f;
+#pragma unroll
+    for (int c = acp_start(g); c < acp_start(g + 1); c++) {
+      const int qx = x + acp_dx(c), qy = y + acp_dy(c);
+      if (qx < 0 || qy < 0 || qx >= a.W || qy >= a.H) continue;
+      const int q = qy * a.W + qx;
+      const float cq = __ldg(&a.cost[q]);
+      if (best < 0 || cq < bc) { best = q; bc = cq; }
+    }
+    pick[g] = best;
+  }
+  float hD[kRegions];
+  uint32_t valid = 0;
+#pragma unroll
+  for (int g = 0; g < kRegions; g++) {
+    hD[g] = 0.f;
+    if (pick[g] < 0) continue;
+    const int q = pick[g];
+    const float4 pq = a.plane[q];
+    const float3 nq = make_float3(pq.x, pq.y, pq.z);
+    const float3 rq = ref_ray(a.Kinv, (float)(q % a.W), (float)(q / a.W));
+    const float d = -pq.w * dot3(nq, rq);          // plane offset, the same at q and x
+    const float den = dot3(nq, ray);
+    if (!(den < 0.f)) continue;
+    const float Dx = -d / den;
+    if (!(Dx > 0.f) || !isfinite(Dx)) continue;
+    float3 c;
+    if (!plane_c(a.Kinv, make_float4(nq.x, nq.y, nq.z, Dx), ray, &c)) continue;
+    sm.cc(g, 0) = c.x;
+    sm.cc(g, 1) = c.y;
+    sm.cc(g, 2) = c.z;
+    hD[g] = Dx;
+    valid |= 1u << g;
+  }
+
+  RefWin rw;
+  load_ref_window<kHalf>(a, x, y, rw);
+
+  // --- Eq. (1): the 8 x N cost matrix (views outer: the 8 hypotheses of a view
+  // fetch neighbouring texels) -------------------------------------------------------
+  for (int j = 0; j < N; j++) {
+    const ViewConst& V = a.v[j];
+#pragma unroll 1
+    for (int g = 0; g < kRegions; g++) {
+      const bool ok = valid >> g & 1u;
+      const float3 c = ok ? make_float3(sm.cc(g, 0), sm.cc(g, 1), sm.cc(g, 2)) : make_float3(0.f, 0.f, 0.f);
+      sm.m(g, j, N) = ncc_cost<kHalf>(V, c, ok, fx, fy, rw, npairs);
+    }
+  }
+
+  // --- Eqs. (2)-(6) ------------------------------------------------------------------
+  uint32_t St;
+  int v;
+  const uint8_t vb = a.vbest[pi];
+  joint_view_selection(a, sm, valid, a.sel[pi], vb == 255 ? -1 : (int)vb, &St, &v);
+  float sw = 0.f;
+  uint32_t wm = 0;
+  for (int j = 0; j < N; j++) {
+    const float wj = sm.wt(j);
+    sw += wj;
+    wm |= (wj > 0.f ? 1u : 0u) << j;
+  }
+  const float inv_sw = 1.f / sw;
+
+  // --- Eq. (7): unified cost; the own plane competes and wins ties -------------------
+  float4 best = a.plane[pi];
+  float3 c;
+  bool ok = plane_c(a.Kinv, best, ray, &c);
+  float bm = 0.f;
+  for (int j = 0; j < N; j++) {   // views with weight 0 are skipped (per-lane predicate)
+    const float wj = sm.wt(j);
+    if (wj > 0.f) bm = fmaf(wj, ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs), bm);
+  }
+  bm *= inv_sw;
+  int choice = 8;
+  float bestD = 0.f;
+#pragma unroll 1
+  for (int g = 0; g < kRegions; g++) {
+    if (!(valid >> g & 1u)) continue;
+    float r = 0.f;
+    for (int j = 0; j < N; j++) {
+      const float wj = sm.wt(j);
+      if (wj > 0.f) r = fmaf(wj, sm.m(g, j, N), r);
+    }
+    r *= inv_sw;
+    if (r < bm) { bm = r; choice = g; }
+  }
+  if (choice < 8) {
+#pragma unroll
+    for (int g = 0; g < kRegions; g++) if (g == choice) bestD = hD[g];
+    const float4 pq = a.plane[pick[choice]];
+    best = make_float4(pq.x, pq.y, pq.z, bestD);
+  }
+
+  // --- Sec. 3.3: refinement with the same weights -------------------------------------
+  const int nc = a.t < 3 ? 1 : kMaxRefine;
+  int bc = -1;
+  float bcm = 0.f;
+#pragma unroll 1
+  for (int ci = 0; ci < nc; ci++) {
+    ok = plane_c(a.Kinv, refine_candidate(a, x, y, best, ray, ci), ray, &c);
+    float m = 0.f;
+    for (int j = 0; j < N; j++) {
+      const float wj = sm.wt(j);
+      if (wj > 0.f) m = fmaf(wj, ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs), m);
+    }
+    m *= inv_sw;
+    if (bc < 0 || m < bcm) { bc = ci; bcm = m; }
+  }
+  if (bc >= 0 && bcm < bm) {
+    bm = bcm;
+    best = refine_candidate(a, x, y, best, ray, bc);
+    choice = 9 + bc;
+  }
+  a.plane[pi] = best;
+  a.cost[pi] = bm;
+  a.sel[pi] = St;
+  a.vbest[pi] = v < 0 ? (uint8_t)255 : (uint8_t)v;
+  a.wmask[pi] = wm;
+  a.choice[pi] = (uint8_t)choice;
+}
+
+// Random initialisation of one pixel (Sec. 2, Gipuma-style random planes):
+// depth uniform in [d_min, d_max], normal uniform on the sphere flipped to
+// face the camera, draws (pixel, 0, 0, 0); the initial cost is the mean of the
+// k smallest per-view costs, summed in ascending order (ties: lower view).
+template <bool kHalf, class A>
+__device__ __forceinline__ void init_pixel(const A& a, PixelArrays& sm, int x, int y, int* npairs) {
+  const int N = a.N;
+  const size_t pi = (size_t)y * a.W + x;
+  const float fx = (float)x, fy = (float)y;
+  const float3 ray = ref_ray(a.Kinv, fx, fy);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)pi, 0u, 0u, 0u), a.key0, a.key1);
+  const float3 n = face_camera(normal_from_uniforms(u01(r.y), u01(r.z)), ray);
+  const float4 pl = make_float4(n.x, n.y, n.z, a.dmin + (a.dmax - a.dmin) * u01(r.x));
+  float3 c;
+  const bool ok = plane_c(a.Kinv, pl, ray, &c);
+  RefWin rw;
+  load_ref_window<kHalf>(a, x, y, rw);
+  for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs);
+  // mean of the k smallest per-view costs, summed in ascending order (ties:
+  // lower view index)
+  const int k = a.k < N ? a.k : N;
+  uint32_t used = 0;
+  float acc = 0.f;
+  for (int r2 = 0; r2 < k; r2++) {
+    int bj = -1;
+    float bmv = 0.f;
+    for (int j = 0; j < N; j++) {
+      const float mj = sm.wt(j);
+      if (!(used >> j & 1u) && (bj < 0 || mj < bmv)) { bj = j; bmv = mj; }
+    }
+    used |= 1u << bj;
+    acc += bmv;
+  }
+  a.plane[pi] = pl;
+  a.cost[pi] = acc / (float)k;
+  a.sel[pi] = 0;
+  a.vbest[pi] = 255;
+  a.wmask[pi] = 0;
+  a.choice[pi] = 8;
+}
+
+}  // namespace upd
+}  // namespace amh

@@ -1,0 +1,80 @@
+"""Parity at the benchmark's full size (3200x2112 reference, 10 sources) in
+the launch configuration bench.py times: the GPU runs a whole colour phase;
+the FP64 oracle recomputes a sample of the updated pixels one by one from the
+same pre-phase state, and the two must keep the same plane with
+|dcost| <= 1e-4 on >= 99.9 % of the sampled pixels that are not near-ties.
+The error statistics are printed (run with -s to see them)."""
+import numpy as np
+import pytest
+
+from parity_utils import COST_TOL, FRACTION, TIE_TOL, same_plane
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_07920_gb300 import amh as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def large_scene(synth_mod):
+    return synth_mod.make_scene("large")
+
+
+def _sample_pixels(W, H, color, n, rng):
+    ys = rng.integers(0, H, n)
+    xs = rng.integers(0, W, n)
+    xs = xs - ((xs + ys + color) & 1)          # move onto the colour
+    xs = np.where(xs < 0, xs + 2, xs)
+    # a few at the borders and corners as well
+    border = np.array([(0, 0), (W - 1, H - 1), (W - 1, 0), (0, H - 1), (W // 2, 0), (0, H // 2), (W - 2, H // 2)])
+    bx, by = border[:, 0], border[:, 1]
+    keep = ((bx + by) & 1) == color
+    return np.concatenate([xs, bx[keep]]), np.concatenate([ys, by[keep]])
+
+
+@pytest.mark.parametrize("t,color", [(1, 0), (4, 1)])
+def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color):
+    sc = large_scene
+    W, H = sc.width, sc.height
+    g = amh.Context.from_scene(sc, seed=23)
+    g.init_random()
+    g.iterate(2)
+    pre = g.get_state()
+    # the same FP32 state in both, iteration index t
+    g.set_state(pre["plane"], pre["cost"], pre["sel"], pre["vbest"], pre["wmask"], pre["choice"], t=t)
+    o = oracle_mod.Oracle.from_scene(sc, seed=23)
+    vb = pre["vbest"].astype(np.int32)
+    vprev = np.where(vb == 255, -1, vb).astype(np.int32)
+    o.set_state(plane=pre["plane"].astype(np.float64), cost=pre["cost"].astype(np.float64), sel=pre["sel"],
+                vprev=vprev, t=t)
+    g.step_phase(color)
+    post = g.get_state()
+    rng = np.random.default_rng(100 + t)
+    xs, ys = _sample_pixels(W, H, color, 1500, rng)
+    n_ok = n_tie = 0
+    dc = []
+    for x, y in zip(xs.tolist(), ys.tolist()):
+        u = o.update_pixel(x, y)
+        gp = post["plane"][y, x].astype(np.float64)
+        same = bool(same_plane(u["plane"], gp)) or u["choice"] == int(post["choice"][y, x])
+        d = abs(u["cost"] - float(post["cost"][y, x]))
+        if same:
+            dc.append(d)
+        if same and d <= COST_TOL:
+            n_ok += 1
+        elif abs(o.score_plane(x, y, gp) - u["cost"]) <= TIE_TOL and d <= TIE_TOL:
+            n_tie += 1
+    n = len(xs)
+    frac = n_ok / max(1, n - n_tie)
+    dc = np.array(dc)
+    print(f"\nfull size t={t} colour={color}: {n} pixels, same plane and |dcost|<=1e-4 on {n_ok}, "
+          f"near-ties {n_tie}; |dcost| on same plane: median {np.median(dc):.2e}, "
+          f"99.9% {np.quantile(dc, 0.999):.2e}, max {dc.max():.2e}")
+    assert frac >= FRACTION, (n_ok, n_tie, n)

@@ -152,3 +152,44 @@ def test_device_buffers_and_stream(amh, tiny_scene):
     h.init_random()
     h.iterate(1)
     np.testing.assert_array_equal(depth.cpu().numpy(), h.read_maps()["depth"])
+
+
+def _fp16_scene(sc):
+    """The same scene with fractional intensities: a view-dependent affine
+    change of the uint8 images, stored as float16.  Both sides read the same
+    float16 values (the oracle in FP64)."""
+    import dataclasses
+    imgs = [(im.astype(np.float32) * (0.61 + 0.07 * v) + 7.3 + 0.35 * v).astype(np.float16)
+            for v, im in enumerate(sc.images)]
+    return dataclasses.replace(sc, images=imgs)
+
+
+def test_fp16_images_init_and_phase_parity(oracle_mod, amh, tiny_scene):
+    sc = _fp16_scene(tiny_scene)
+    o, g = _pair(oracle_mod, amh, sc, seed=61)
+    assert g.params.flags & amh.AMH_FLAG_IMAGES_F16
+    o.init_random()
+    g.init_random()
+    so, sg = o.get_state(), g.get_state()
+    d = np.abs(so["cost"] - sg["cost"])
+    assert (d <= COST_TOL).mean() >= FRACTION
+    o.iterate(2)
+    st = o.get_state()
+    for t, color in ((1, 0), (4, 1)):
+        st["t"] = t
+        r = phase_check(o, g, st, color)
+        assert r["frac_ok_nontie"] >= FRACTION, r
+
+
+def test_fp16_and_uint8_agree_on_integer_images(amh, tiny_scene):
+    """uint8 values are exact in FP16: both storages give the same update."""
+    import dataclasses
+    sc16 = dataclasses.replace(tiny_scene, images=[im.astype(np.float16) for im in tiny_scene.images])
+    a = amh.Context.from_scene(tiny_scene, seed=62)
+    b = amh.Context.from_scene(sc16, seed=62)
+    for c in (a, b):
+        c.init_random()
+        c.step_phase(0)
+    sa, sb = a.get_state(), b.get_state()
+    assert (np.abs(sa["cost"] - sb["cost"]) <= COST_TOL).mean() >= FRACTION
+    assert same_plane(sa["plane"].astype(np.float64), sb["plane"].astype(np.float64), 1e-4, 1e-6).mean() >= 0.995
