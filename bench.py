@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-form measurement")
     return ap.parse_args()
 
 
@@ -318,6 +319,10 @@ def run_ours(args):
                "path": "amh_create from pinned host images + init + 6 iterations + amh_read_maps to pinned "
                        "host + amh_destroy"}
 
+    extras = {}
+    if not args.no_extras:
+        extras["batched_ring20"] = bench_batch(args, dist)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, info = cpu_oracle_rate(sc, args.cpu_seconds)
@@ -333,7 +338,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ray-cast scene)",
             "config": workload_config(sc) | {"parallelism": f"replicas{world}: one reference view per GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "extras": extras,
             "clocks": clocks, "gpu_launches": args.steps * (1 + 2 * ITERS),
             "pairs_per_step": pairs_init + pairs_phase,
         }
@@ -342,6 +347,44 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def bench_batch(args, dist):
+    """Batched form: the 20-camera ring, every view the reference with its 10
+    nearest views as sources (8 x 1920x1080, 6 x 2560x1440, 6 x 3200x2112), one
+    persistent launch per colour phase, init + 6 iterations replayed from a
+    CUDA graph, tile variant picked by the autotuner."""
+    import torch
+    from paper_1805_07920_gb300 import amh, synth
+    sc = synth.make_scene("ring20")
+    n = len(sc.cams)
+    refs = list(range(n))
+    srcs = [synth.ring_sources(r, n, 10) for r in refs]
+    p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=SEED)
+    b = amh.Batch(sc.cams, sc.images, refs, srcs, p)
+    chosen, tune_ms = b.autotune(iters=1)
+    for _ in range(max(1, args.warmup)):
+        b.run(ITERS)
+    b.synchronize()
+    b.pair_count(reset=True)
+    b.run(ITERS)
+    pairs = b.pair_count(reset=True)
+    steps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    b.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.run(ITERS)
+    b.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    px = sum(w * h for (w, h, _) in b.sizes)
+    b.close()
+    return {"metric": "Mpixel-iterations/s over all 20 references", "unit": UNIT,
+            "value": round(px * ITERS * steps / (ms / 1e3) / 1e6, 3), "ms_per_batch": round(ms / steps, 3),
+            "pixels_per_iteration": px, "pairs_per_batch": pairs, "launches_per_batch": 1 + 2 * ITERS,
+            "tile_variant": ["16x16", "32x8", "64x4"][chosen],
+            "autotune_ms": [round(float(m), 3) for m in tune_ms], "timing": "host wall clock around graph launches"}
 
 
 def main():

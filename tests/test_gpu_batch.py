@@ -91,6 +91,6 @@ def test_autotune_picks_a_variant(amh, ring, synth_mod):
 
 def test_batch_rejects_bad_lists(amh, ring):
     with pytest.raises(amh.AmhError):
-        amh.Batch(ring.cams, ring.images, [0, 1], [[1, 2], [3]])      # ref 1 lists itself
+        amh.Batch(ring.cams, ring.images, [0, 1], [[1, 2], [1, 3]])   # ref 1 lists itself
     with pytest.raises(amh.AmhError):
         amh.Batch(ring.cams, ring.images, [0], [[]])                  # no source
