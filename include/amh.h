@@ -214,6 +214,83 @@ AMH_API const char* amh_batch_last_error(const amh_batch* batch);
 AMH_API void amh_batch_destroy(amh_batch* batch);
 
 
+/* ------------------------------------------------------------------------
+ * Learned proposal (this project's extension; the paper trains no network
+ * and proposes planes only by propagation (Sec. 3.1) and refinement
+ * (Sec. 3.4)).  A 4-level convolutional encoder-decoder (3x3 convolutions
+ * 16-32-64-96-128 channels, 2x2 average pooling, nearest upsampling,
+ * additive skips; BF16 weights and activations, FP32 accumulation on tensor
+ * cores) reads a context's state on the half-resolution grid (X, Y) =
+ * (x/2, y/2) -- intensity, log depth, normal and cost of pixel (2X, 2Y) --
+ * and predicts the residuals (log-depth change, normal change) towards the
+ * converged plane.  amh_net_propose hands the predicted plane of each 2 x 2
+ * block to the context: its phases then score it with the unchanged
+ * matching cost (Eq. 8) under the pixel's view weights (Eqs. 2-7) as one
+ * more refinement candidate (winning choice code 15), so the plain method
+ * stays the arbiter.  Training runs on the same kernels: amh_net_features
+ * (inputs) -> more plain iterations -> amh_net_targets -> amh_net_forward
+ * -> amh_net_backward (L1 loss, every gradient) -> amh_net_adam.
+ *
+ * Layouts: features height2 x width2 x 16 floats (6 used); outputs height2
+ * x width2 x 16 floats (4 used); targets height2 x width2 x 4 floats plus a
+ * uint8 mask; weights of layer L (0..7 = e1 e2 e3 e4 d3 d2 d1 out) 9 x Cout
+ * x Cin floats, tap 3 (dy + 1) + (dx + 1), biases Cout floats.  Host
+ * buffers are the caller's.  Calls run on the stream given at creation;
+ * those that return host data synchronise it.  Errors: AMH_EINVAL for NULL
+ * handles / buffers, an unknown layer or a context larger than the network;
+ * AMH_ENOMEM / AMH_ECUDA from the runtime, with amh_net_last_error.
+ * ------------------------------------------------------------------------ */
+typedef struct amh_net amh_net;
+
+/* Network for half-resolution inputs of width2 x height2 (positive
+ * multiples of 8, at most 2^24 pixels); a W x H reference needs at least
+ * ceil(W/2) x ceil(H/2).  He-normal weights drawn from the seed (output
+ * layer scaled by 0.1), zero biases, zero Adam moments. */
+AMH_API int amh_net_create(amh_net** out, int32_t width2, int32_t height2, uint64_t seed,
+                           void* stream);
+/* FP32 master weights w and biases b of one layer: read into the host
+ * buffers (set = 0) or written from them (set != 0; either may be NULL). */
+AMH_API int amh_net_params(amh_net* net, int32_t layer, float* w, float* b, int32_t set);
+/* Weight and bias gradients of the last amh_net_backward, same layout. */
+AMH_API int amh_net_grads(amh_net* net, int32_t layer, float* gw, float* gb);
+/* Features from host memory (stored as BF16). */
+AMH_API int amh_net_set_input(amh_net* net, const float* x0);
+/* Features from the context's current state; also keeps that state's planes
+ * as the base the outputs are residuals of. */
+AMH_API int amh_net_features(amh_net* net, amh_ctx* ctx);
+/* Targets: the context's current planes minus the kept base planes, where
+ * the current cost is below cost_max (mask 1), else 0 (mask 0). */
+AMH_API int amh_net_targets(amh_net* net, amh_ctx* ctx, float cost_max);
+/* Targets and mask from host memory. */
+AMH_API int amh_net_set_targets(amh_net* net, const float* target, const uint8_t* mask);
+/* Forward pass; out (may be NULL) receives the outputs. */
+AMH_API int amh_net_forward(amh_net* net, float* out);
+/* L1 loss of the last forward against the targets (sum over the 4 used
+ * channels, mean over masked pixels) into *loss (may be NULL), and every
+ * weight and bias gradient. */
+AMH_API int amh_net_backward(amh_net* net, float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. */
+AMH_API int amh_net_adam(amh_net* net, float lr);
+/* Proposals from the last forward for the context's following phases; the
+ * network must outlive their use (or call amh_clear_proposal first). */
+AMH_API int amh_net_propose(amh_net* net, amh_ctx* ctx);
+/* Stop scoring proposals in the context. */
+AMH_API int amh_clear_proposal(amh_ctx* ctx);
+/* Internal tensors, for element-wise checks of every operation: which =
+ * 0..17 the forward tensors x0 e1 in_e2 e2 in_e3 e3 in_e4 e4 in_d3 r3 d3
+ * in_d2 r2 d2 in_d1 r1 d1 out (in_* = pooled / upsampled inputs, r* = a
+ * decoder layer's ReLU output before its skip; BF16 ones widened to FP32),
+ * 32 + L the gradient at layer L's output after its ReLU mask (FP32, from the
+ * last amh_net_backward).  Layout (H, W, C) of that level.  With out = NULL
+ * the element count is written to *count; otherwise *count must equal it. */
+AMH_API int amh_net_read(amh_net* net, int32_t which, float* out, int64_t* count);
+/* Wait for the network's work. */
+AMH_API int amh_net_synchronize(amh_net* net);
+/* Message of the last failure (NULL net: of the last failed create). */
+AMH_API const char* amh_net_last_error(const amh_net* net);
+/* Free everything; NULL is allowed. */
+AMH_API void amh_net_destroy(amh_net* net);
+
 #define AMH_NOALLOC_MAX_PIXELS 262144
 
 /* amh_read_maps without any allocation (the paper has no counterpart: this

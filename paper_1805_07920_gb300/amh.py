@@ -28,7 +28,10 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_read_maps_noalloc", "amh_batch_create", "amh_batch_init_random", "amh_batch_step_phase",
            "amh_batch_iterate", "amh_batch_run", "amh_batch_set_variant", "amh_batch_autotune",
            "amh_batch_info", "amh_batch_get_state", "amh_batch_pair_count", "amh_batch_synchronize",
-           "amh_batch_last_error", "amh_batch_destroy"]
+           "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
+           "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
+           "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
+           "amh_net_last_error", "amh_net_destroy"]
 
 
 class AmhError(RuntimeError):
@@ -388,3 +391,167 @@ class Batch:
         self._check(_batch_lib().amh_batch_get_state(self.ctx, int(r), ctypes.byref(s), AMH_MEM_HOST))
         st["t"] = s.t
         return st
+
+
+# ---------------------------------------------------------------------------
+# learned proposal network
+# ---------------------------------------------------------------------------
+NET_LAYERS = [("e1", 16, 32), ("e2", 32, 64), ("e3", 64, 96), ("e4", 96, 128),
+              ("d3", 128, 96), ("d2", 96, 64), ("d1", 64, 32), ("out", 32, 16)]
+_NET_READY = False
+
+
+def _net_lib():
+    global _NET_READY
+    L = lib()
+    if not _NET_READY:
+        _fp = ctypes.POINTER(ctypes.c_float)
+        L.amh_net_create.argtypes = [ctypes.POINTER(_vp), _i32, _i32, ctypes.c_uint64, _vp]
+        L.amh_net_params.argtypes = [_vp, _i32, _vp, _vp, _i32]
+        L.amh_net_grads.argtypes = [_vp, _i32, _vp, _vp]
+        L.amh_net_set_input.argtypes = [_vp, _vp]
+        L.amh_net_features.argtypes = [_vp, _vp]
+        L.amh_net_targets.argtypes = [_vp, _vp, ctypes.c_float]
+        L.amh_net_set_targets.argtypes = [_vp, _vp, _vp]
+        L.amh_net_forward.argtypes = [_vp, _vp]
+        L.amh_net_backward.argtypes = [_vp, _fp]
+        L.amh_net_adam.argtypes = [_vp, ctypes.c_float]
+        L.amh_net_read.argtypes = [_vp, _i32, _vp, ctypes.POINTER(ctypes.c_int64)]
+        L.amh_net_propose.argtypes = [_vp, _vp]
+        L.amh_clear_proposal.argtypes = [_vp]
+        L.amh_net_synchronize.argtypes = [_vp]
+        L.amh_net_last_error.argtypes = [_vp]
+        L.amh_net_last_error.restype = ctypes.c_char_p
+        L.amh_net_destroy.argtypes = [_vp]
+        L.amh_net_destroy.restype = None
+        _NET_READY = True
+    return L
+
+
+def net_size_for(width, height):
+    """Network input size for a width x height reference: the (x/2, y/2) grid
+    rounded up to multiples of 8."""
+    r8 = lambda v: (v + 7) // 8 * 8
+    return r8((width + 1) // 2), r8((height + 1) // 2)
+
+
+class Net:
+    """The learned proposal network (``amh_net_*``)."""
+
+    def __init__(self, width2, height2, seed=0, stream=None):
+        L = _net_lib()
+        self.ctx = _vp()
+        if stream is None:
+            stream = _current_stream()
+        rc = L.amh_net_create(ctypes.byref(self.ctx), int(width2), int(height2), ctypes.c_uint64(seed), stream)
+        if rc != AMH_OK:
+            raise AmhError(rc, L.amh_net_last_error(None).decode())
+        self.w2, self.h2 = int(width2), int(height2)
+
+    def _check(self, rc):
+        if rc != AMH_OK:
+            raise AmhError(rc, _net_lib().amh_net_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            _net_lib().amh_net_destroy(self.ctx)
+            self.ctx = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = {}
+        for i, (name, cin, cout) in enumerate(NET_LAYERS):
+            w = np.zeros((9, cout, cin), np.float32)
+            b = np.zeros(cout, np.float32)
+            self._check(_net_lib().amh_net_params(self.ctx, i, _ptr(w), _ptr(b), 0))
+            out[name] = (w, b)
+        return out
+
+    def set_params(self, params):
+        for i, (name, cin, cout) in enumerate(NET_LAYERS):
+            w = np.ascontiguousarray(params[name][0], np.float32).reshape(9, cout, cin)
+            b = np.ascontiguousarray(params[name][1], np.float32).reshape(cout)
+            self._check(_net_lib().amh_net_params(self.ctx, i, _ptr(w), _ptr(b), 1))
+
+    def get_grads(self):
+        out = {}
+        for i, (name, cin, cout) in enumerate(NET_LAYERS):
+            w = np.zeros((9, cout, cin), np.float32)
+            b = np.zeros(cout, np.float32)
+            self._check(_net_lib().amh_net_grads(self.ctx, i, _ptr(w), _ptr(b)))
+            out[name] = (w, b)
+        return out
+
+    def set_input(self, x0):
+        x = np.ascontiguousarray(x0, np.float32).reshape(self.h2, self.w2, 16)
+        self._check(_net_lib().amh_net_set_input(self.ctx, _ptr(x)))
+
+    def set_targets(self, target, mask):
+        t = np.ascontiguousarray(target, np.float32).reshape(self.h2, self.w2, 4)
+        m = np.ascontiguousarray(mask, np.uint8).reshape(self.h2, self.w2)
+        self._check(_net_lib().amh_net_set_targets(self.ctx, _ptr(t), _ptr(m)))
+
+    def features(self, ctx: Context):
+        self._check(_net_lib().amh_net_features(self.ctx, ctx.ctx))
+
+    def targets(self, ctx: Context, cost_max=0.5):
+        self._check(_net_lib().amh_net_targets(self.ctx, ctx.ctx, float(cost_max)))
+
+    def forward(self, want_output=False):
+        out = np.zeros((self.h2, self.w2, 16), np.float32) if want_output else None
+        self._check(_net_lib().amh_net_forward(self.ctx, _ptr(out) if want_output else None))
+        return out
+
+    def backward(self):
+        loss = ctypes.c_float()
+        self._check(_net_lib().amh_net_backward(self.ctx, ctypes.byref(loss)))
+        return loss.value
+
+    def adam(self, lr):
+        self._check(_net_lib().amh_net_adam(self.ctx, float(lr)))
+
+    def propose(self, ctx: Context):
+        self._check(_net_lib().amh_net_propose(self.ctx, ctx.ctx))
+
+    # name -> (level, channels); level k is (height2 >> k, width2 >> k)
+    NET_TENSORS = {"x0": (0, 16), "e1": (0, 32), "in_e2": (1, 32), "e2": (1, 64), "in_e3": (2, 64), "e3": (2, 96),
+                   "in_e4": (3, 96), "e4": (3, 128), "in_d3": (2, 128), "r3": (2, 96), "d3": (2, 96),
+                   "in_d2": (1, 96), "r2": (1, 64), "d2": (1, 64), "in_d1": (0, 64), "r1": (0, 32), "d1": (0, 32),
+                   "out": (0, 16)}
+    LAYER_LEVEL = {"e1": 0, "e2": 1, "e3": 2, "e4": 3, "d3": 2, "d2": 1, "d1": 0, "out": 0}
+
+    def read(self, name):
+        """An internal tensor as float32 (H, W, C): a forward tensor of
+        NET_TENSORS, or "dy:<layer>" for the gradient at that layer's output
+        after its ReLU mask (from the last backward)."""
+        names = [n for n, _, _ in NET_LAYERS]
+        if name.startswith("dy:"):
+            L = names.index(name[3:])
+            which, level, ch = 32 + L, self.LAYER_LEVEL[name[3:]], NET_LAYERS[L][2]
+        else:
+            which = list(self.NET_TENSORS).index(name)
+            level, ch = self.NET_TENSORS[name]
+        cnt = ctypes.c_int64((self.h2 >> level) * (self.w2 >> level) * ch)
+        out = np.zeros(cnt.value, np.float32)
+        self._check(_net_lib().amh_net_read(self.ctx, which, _ptr(out), ctypes.byref(cnt)))
+        return out.reshape(self.h2 >> level, self.w2 >> level, ch)
+
+    def synchronize(self):
+        self._check(_net_lib().amh_net_synchronize(self.ctx))
+
+    def save(self, path):
+        p = self.get_params()
+        np.savez_compressed(path, **{f"{k}_w": v[0] for k, v in p.items()}, **{f"{k}_b": v[1] for k, v in p.items()})
+
+    def load(self, path):
+        z = np.load(path)
+        self.set_params({name: (z[f"{name}_w"], z[f"{name}_b"]) for name, _, _ in NET_LAYERS})
+
+
+def clear_proposal(ctx: Context):
+    ctx._check(_net_lib().amh_clear_proposal(ctx.ctx))

@@ -48,6 +48,8 @@ struct RefArgs {
   uint8_t* vbest;
   uint32_t* wmask;
   uint8_t* choice;
+  const float4* prop;    // no learned proposals in the batched form (null)
+  int prop_w, prop_h;
   const ViewConst* vt;   // N views in global memory
   int tile0, tiles_x, tiles;
   ViewConst v[kMaxSrc];  // copied from vt into shared memory per item

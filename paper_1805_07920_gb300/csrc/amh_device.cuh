@@ -55,6 +55,8 @@ struct PhaseArgs {
   uint32_t* wmask;
   uint8_t* choice;
   unsigned long long* pairs; // kPairCounters striped (hypothesis, view) evaluation counters
+  const float4* prop;        // learned proposals (n, d) on the (x/2, y/2) grid, or null
+  int prop_w, prop_h;
   ViewConst v[kMaxSrc];
 };
 

@@ -1,0 +1,745 @@
+// amh_learned.cu -- the learned proposal network (this project's extension):
+// a 4-level convolutional encoder-decoder that reads the half-resolution
+// state of the checkerboard update (reference intensity, log depth, normal,
+// cost) and proposes one plane per pixel; the phase kernel scores that plane
+// with the unchanged matching cost (Eq. 8) and view weights (Eqs. 2-7) as one
+// more candidate, so the plain method stays the arbiter.
+//
+// Kernels: 3x3 convolution forward on tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation, fused bias / ReLU / skip add), the data
+// gradient as the same convolution with flipped, transposed weights, the
+// weight gradient in FP32, 2x2 average pooling, nearest upsampling, the L1
+// loss, Adam, and the feature / head / proposal conversions.
+//
+// Layout: activations (H, W, C) with C a multiple of 16, BF16 between
+// layers; conv weights (9, Cout, Cin) BF16 (FP32 master copy for Adam), tap
+// t = 3 (dy + 1) + (dx + 1).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "amh.h"
+#include "amh_ctx.h"
+#include "amh_device.cuh"
+
+namespace amh {
+namespace {
+
+constexpr int kLayers = 8;
+struct LayerDef { int cin, cout, relu; };
+// e1 e2 e3 e4 d3 d2 d1 out
+constexpr LayerDef kNet[kLayers] = {{16, 32, 1}, {32, 64, 1}, {64, 96, 1}, {96, 128, 1},
+                                    {128, 96, 1}, {96, 64, 1}, {64, 32, 1}, {32, 16, 0}};
+
+// ---------------------------------------------------------------------------
+// tensor-core 3x3 convolution: a block computes 64 pixels of one row x 32
+// output channels; warp w takes pixels 16 w .. 16 w + 15 (one m16 tile) and
+// the 4 n8 tiles.  The block's weights sit in shared memory, rows padded by 8
+// BF16 so the B-fragment loads are conflict-free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct ConvArgs {
+  const __nv_bfloat16* x;    // (H, W, Cin)
+  const __nv_bfloat16* w;    // (9, Cout, Cin)
+  const float* bias;         // Cout or null
+  const __nv_bfloat16* skip; // (H, W, Cout) added after the ReLU, or null
+  __nv_bfloat16* y16;        // (H, W, Cout) BF16 output (after ReLU + skip), or null
+  __nv_bfloat16* r16;        // (H, W, Cout) ReLU output before the skip, or null
+  float* y32;                // (H, W, Cout) FP32 output, or null
+  int H, W, Cin, Cout, relu;
+};
+
+__global__ void __launch_bounds__(128) conv3x3_fwd_kernel(const ConvArgs a) {
+  extern __shared__ __nv_bfloat16 ws[];   // [9][32][Cin + 8]
+  const int ld = a.Cin + 8;
+  const int co0 = blockIdx.z * 32;
+  const int y = blockIdx.y, x0 = blockIdx.x * 64;
+  for (int i = threadIdx.x; i < 9 * 32 * a.Cin; i += blockDim.x) {
+    const int t = i / (32 * a.Cin), r = (i / a.Cin) % 32, ci = i % a.Cin;
+    const int co = co0 + r;
+    ws[(t * 32 + r) * ld + ci] = co < a.Cout ? a.w[((size_t)t * a.Cout + co) * a.Cin + ci] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int px0 = x0 + warp * 16 + g, px1 = px0 + 8;
+  float acc[4][4];
+#pragma unroll
+  for (int n = 0; n < 4; n++)
+#pragma unroll
+    for (int e = 0; e < 4; e++) acc[n][e] = 0.f;
+  for (int t = 0; t < 9; t++) {
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    const int yy = y + dy;
+    const int xa = px0 + dx, xb = px1 + dx;
+    const bool rowok = yy >= 0 && yy < a.H;
+    const bool oka = rowok && xa >= 0 && xa < a.W, okb = rowok && xb >= 0 && xb < a.W;
+    const uint32_t* pa = reinterpret_cast<const uint32_t*>(a.x + (oka ? ((size_t)yy * a.W + xa) * a.Cin : 0));
+    const uint32_t* pb = reinterpret_cast<const uint32_t*>(a.x + (okb ? ((size_t)yy * a.W + xb) * a.Cin : 0));
+    const __nv_bfloat16* wt = ws + (size_t)t * 32 * ld;
+    for (int c0 = 0; c0 < a.Cin; c0 += 16) {
+      uint32_t af[4];
+      af[0] = oka ? __ldg(pa + (c0 >> 1) + tq) : 0u;
+      af[1] = okb ? __ldg(pb + (c0 >> 1) + tq) : 0u;
+      af[2] = oka ? __ldg(pa + (c0 >> 1) + tq + 4) : 0u;
+      af[3] = okb ? __ldg(pb + (c0 >> 1) + tq + 4) : 0u;
+#pragma unroll
+      for (int n = 0; n < 4; n++) {
+        const __nv_bfloat16* wr = wt + (n * 8 + g) * ld + c0 + 2 * tq;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 8);
+        mma_bf16(acc[n], af, b0, b1);
+      }
+    }
+  }
+  // epilogue: (row g -> pixel px0, row g + 8 -> px1), columns 2 tq, 2 tq + 1
+#pragma unroll
+  for (int n = 0; n < 4; n++) {
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int px = e < 2 ? px0 : px1;
+      const int co = co0 + n * 8 + 2 * tq + (e & 1);
+      if (px >= a.W || co >= a.Cout) continue;
+      float v = acc[n][e] + (a.bias ? a.bias[co] : 0.f);
+      if (a.relu) v = fmaxf(v, 0.f);
+      const size_t o = ((size_t)y * a.W + px) * a.Cout + co;
+      if (a.r16) a.r16[o] = __float2bfloat16(v);
+      if (a.skip) v = __bfloat162float(__float2bfloat16(v)) + __bfloat162float(a.skip[o]);
+      if (a.y16) a.y16[o] = __float2bfloat16(v);
+      if (a.y32) a.y32[o] = v;
+    }
+  }
+}
+
+// weight gradient in FP32: a block owns one tap and a 32 x 32 (co, ci) tile
+// and sums the chunks of kWgChunk pixels chunk0, chunk0 + stride, ...; warp
+// w takes co 4w .. 4w + 3, lane = ci.  The partial sums meet in dw / db by
+// atomics (one per block and output).
+constexpr int kWgChunk = 128;
+__global__ void __launch_bounds__(256) conv3x3_wgrad_kernel(const __nv_bfloat16* __restrict__ x,
+                                                           const float* __restrict__ dy, float* dw, float* db,
+                                                           int H, int W, int Cin, int Cout) {
+  __shared__ float sdy[kWgChunk][33];
+  __shared__ float sx[kWgChunk][33];
+  const int t = blockIdx.z % 9, stride = gridDim.z / 9;
+  const int co0 = blockIdx.y * 32, ci0 = blockIdx.x * 32;
+  const int oy = t / 3 - 1, ox = t % 3 - 1;
+  const int np = H * W, nchunks = (np + kWgChunk - 1) / kWgChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float bsum = 0.f;
+  for (int chunk = blockIdx.z / 9; chunk < nchunks; chunk += stride) {
+    const int p0 = chunk * kWgChunk;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWgChunk * 32; i += blockDim.x) {
+      const int pp = i / 32, c = i % 32;
+      const int p = p0 + pp;
+      float vdy = 0.f, vx = 0.f;
+      if (p < np) {
+        const int py = p / W, pxx = p % W;
+        if (co0 + c < Cout) vdy = dy[(size_t)p * Cout + co0 + c];
+        const int qy = py + oy, qx = pxx + ox;
+        if (ci0 + c < Cin && qy >= 0 && qy < H && qx >= 0 && qx < W)
+          vx = __bfloat162float(x[((size_t)qy * W + qx) * Cin + ci0 + c]);
+      }
+      sdy[pp][c] = vdy;
+      sx[pp][c] = vx;
+    }
+    __syncthreads();
+    for (int pp = 0; pp < kWgChunk; pp++) {
+      const float xv = sx[pp][lane];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fmaf(sdy[pp][warp * 4 + q], xv, acc[q]);
+    }
+    if (warp == 0)
+      for (int pp = 0; pp < kWgChunk; pp++) bsum += sdy[pp][lane];
+  }
+  const int ci = ci0 + lane;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int co = co0 + warp * 4 + q;
+    if (co < Cout && ci < Cin) atomicAdd(&dw[((size_t)t * Cout + co) * Cin + ci], acc[q]);
+  }
+  if (t == 4 && blockIdx.x == 0 && warp == 0 && co0 + lane < Cout) atomicAdd(&db[co0 + lane], bsum);
+}
+
+// weights (9, Cout, Cin) -> data-gradient weights (9, Cin, Cout), taps flipped
+__global__ void flip_transpose_kernel(const __nv_bfloat16* w, __nv_bfloat16* wd, int Cin, int Cout) {
+  const int n = 9 * Cin * Cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int t = i / (Cin * Cout), ci = (i / Cout) % Cin, co = i % Cout;
+    wd[i] = w[((size_t)(8 - t) * Cout + co) * Cin + ci];
+  }
+}
+
+__global__ void pool2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int H, int W, int C) {
+  const int Ho = H / 2, Wo = W / 2;
+  const size_t n = (size_t)Ho * Wo * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = i % C, p = (int)(i / C), oy = p / Wo, ox = p % Wo;
+    const size_t b = ((size_t)(2 * oy) * W + 2 * ox) * C + c;
+    const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (size_t)W * C]) +
+                    __bfloat162float(x[b + (size_t)W * C + C]);
+    y[i] = __float2bfloat16(0.25f * s);
+  }
+}
+__global__ void pool2_bwd_add_kernel(const float* d, float* dx, int H, int W, int C) {   // dx += pool'^T d
+  const size_t n = (size_t)H * W * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = i % C, p = (int)(i / C), yy = p / W, xx = p % W;
+    dx[i] += 0.25f * d[((size_t)(yy / 2) * (W / 2) + xx / 2) * C + c];
+  }
+}
+__global__ void up2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int Ho, int Wo, int C) {  // (Ho, Wo) output
+  const size_t n = (size_t)Ho * Wo * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = i % C, p = (int)(i / C), yy = p / Wo, xx = p % Wo;
+    y[i] = x[((size_t)(yy / 2) * (Wo / 2) + xx / 2) * C + c];
+  }
+}
+__global__ void up2_bwd_kernel(const float* d, float* dx, int H, int W, int C) {   // (H, W) = input size
+  const size_t n = (size_t)H * W * C;
+  const int Wo = 2 * W;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = i % C, p = (int)(i / C), yy = p / W, xx = p % W;
+    const size_t b = ((size_t)(2 * yy) * Wo + 2 * xx) * C + c;
+    dx[i] = d[b] + d[b + C] + d[b + (size_t)Wo * C] + d[b + (size_t)Wo * C + C];
+  }
+}
+// g (FP32) times the ReLU mask of r, optionally also into a BF16 copy
+__global__ void relu_mask_kernel(const float* g, const __nv_bfloat16* r, float* out, __nv_bfloat16* out16, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = __bfloat162float(r[i]) > 0.f ? g[i] : 0.f;
+    out[i] = v;
+    if (out16) out16[i] = __float2bfloat16(v);
+  }
+}
+__global__ void bf16_to_f32_kernel(const __nv_bfloat16* g, float* o, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = __bfloat162float(g[i]);
+}
+__global__ void to_bf16_kernel(const float* g, __nv_bfloat16* o, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = __float2bfloat16(g[i]);
+}
+
+// L1 loss over the 4 used output channels of the masked pixels and its
+// gradient; loss accumulated in *loss (sum; the host divides by the count)
+__global__ void l1_loss_kernel(const float* out, const float* target, const uint8_t* mask, float* dout, float* loss,
+                               int np, float inv_n) {
+  float s = 0.f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    for (int c = 0; c < 16; c++) {
+      float g = 0.f;
+      if (c < 4 && mask[p]) {
+        const float d = out[(size_t)p * 16 + c] - target[(size_t)p * 4 + c];
+        s += fabsf(d);
+        g = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * inv_n;
+      }
+      dout[(size_t)p * 16 + c] = g;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_n);
+}
+
+__global__ void adam_kernel(float* w, float* m, float* v, const float* g, __nv_bfloat16* w16, int n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (w16) w16[i] = __float2bfloat16(wi);
+  }
+}
+
+// Features of half-resolution pixel (X, Y), read at full-resolution pixel
+// (2X, 2Y): intensity / 255 - 0.5, normalised log depth, normal, cost / 2,
+// zeros up to 16 channels.  Also keeps the input plane for the head.
+__global__ void features_kernel(const void* ref, int ref_half, const float4* plane, const float* cost, int W, int H,
+                                int w2, int h2, float lmid, float lscale, __nv_bfloat16* x0, float4* pin) {
+  const int n = w2 * h2;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int X = p % w2, Y = p / w2;
+    const int x = min(2 * X, W - 1), y = min(2 * Y, H - 1);
+    const size_t q = (size_t)y * W + x;
+    const float I = ref_half ? __half2float(reinterpret_cast<const __half*>(ref)[q])
+                             : (float)reinterpret_cast<const uint8_t*>(ref)[q];
+    const float4 pl = plane[q];
+    const float f[6] = {I / 255.f - 0.5f, (logf(fmaxf(pl.w, 1e-6f)) - lmid) * lscale, pl.x, pl.y, pl.z,
+                        cost[q] * 0.5f};
+    for (int c = 0; c < 16; c++) x0[(size_t)p * 16 + c] = __float2bfloat16(c < 6 ? f[c] : 0.f);
+    pin[p] = pl;
+  }
+}
+// targets: (log D_final - log D_in, n_final - n_in) where the final cost is
+// below cmax (confident pixels)
+__global__ void targets_kernel(const float4* plane, const float* cost, const float4* pin, int W, int H, int w2,
+                               int h2, float cmax, float* target, uint8_t* mask) {
+  const int n = w2 * h2;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int X = p % w2, Y = p / w2;
+    const int x = min(2 * X, W - 1), y = min(2 * Y, H - 1);
+    const size_t q = (size_t)y * W + x;
+    const float4 pf = plane[q], pi = pin[p];
+    const bool ok = cost[q] < cmax && pf.w > 0.f && pi.w > 0.f;
+    target[(size_t)p * 4 + 0] = ok ? logf(pf.w) - logf(pi.w) : 0.f;
+    target[(size_t)p * 4 + 1] = ok ? pf.x - pi.x : 0.f;
+    target[(size_t)p * 4 + 2] = ok ? pf.y - pi.y : 0.f;
+    target[(size_t)p * 4 + 3] = ok ? pf.z - pi.z : 0.f;
+    mask[p] = ok ? 1 : 0;
+  }
+}
+// head: proposal plane of half-resolution pixel (X, Y) as (n, d) with
+// n . X + d = 0, from the input plane and the predicted residuals, valid when
+// it faces the camera at full-resolution pixel (2X, 2Y)
+__global__ void head_kernel(const float* out, const float4* pin, int W, int H, int w2, int h2, PhaseArgs geo,
+                            float4* prop) {
+  const int n = w2 * h2;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int X = p % w2, Y = p / w2;
+    const float x = (float)min(2 * X, W - 1), y = (float)min(2 * Y, H - 1);
+    const float4 pi = pin[p];
+    const float* o = out + (size_t)p * 16;
+    const float D = pi.w * expf(fminf(fmaxf(o[0], -3.f), 3.f));
+    float3 nn = make_float3(pi.x + o[1], pi.y + o[2], pi.z + o[3]);
+    const float l = sqrtf(dot3(nn, nn));
+    const float3 ray = ref_ray(geo.Kinv, x, y);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l > 1e-6f && pi.w > 0.f && isfinite(D)) {
+      nn = face_camera(make_float3(nn.x / l, nn.y / l, nn.z / l), ray);
+      const float d = -D * dot3(nn, ray);
+      if (d > 0.f && isfinite(d)) r = make_float4(nn.x, nn.y, nn.z, d);
+    }
+    prop[p] = r;
+  }
+}
+
+int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
+
+}  // namespace
+}  // namespace amh
+
+using namespace amh;
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct amh_net {
+  int w2 = 0, h2 = 0;                     // network input size (half resolution)
+  cudaStream_t stream = nullptr;
+  // parameters per layer: FP32 master, BF16 copy, Adam moments, gradients
+  float* wm[kLayers] = {};
+  float* bm[kLayers] = {};
+  __nv_bfloat16* w16[kLayers] = {};
+  __nv_bfloat16* wd16[kLayers] = {};      // data-gradient weights
+  float *mw[kLayers] = {}, *vw[kLayers] = {}, *mb[kLayers] = {}, *vb[kLayers] = {};
+  float *gw[kLayers] = {}, *gb[kLayers] = {};
+  int step = 0;
+  // activations (BF16) and gradient buffers (FP32)
+  __nv_bfloat16 *x0 = nullptr, *e1 = nullptr, *in_e2 = nullptr, *e2 = nullptr, *in_e3 = nullptr, *e3 = nullptr,
+                *in_e4 = nullptr, *e4 = nullptr, *in_d3 = nullptr, *r3 = nullptr, *d3 = nullptr, *in_d2 = nullptr,
+                *r2 = nullptr, *d2 = nullptr, *in_d1 = nullptr, *r1 = nullptr, *d1 = nullptr, *g16 = nullptr;
+  float* out = nullptr;
+  float* target = nullptr;
+  uint8_t* mask = nullptr;
+  float4* pin = nullptr;
+  float4* prop = nullptr;
+  // backward: dy[L] = gradient at layer L's output after its ReLU mask (FP32),
+  // gA / gB scratch, gE1..gE3 gradients arriving at e1..e3 through the skips
+  float* dy[kLayers] = {};
+  float *gA = nullptr, *gB = nullptr, *gE1 = nullptr, *gE2 = nullptr, *gE3 = nullptr;
+  float* loss = nullptr;
+  size_t maxel = 0;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+thread_local std::string g_net_err;
+int nfail(amh_net* n, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (n) n->err = buf; else g_net_err = buf;
+  return code;
+}
+template <typename T>
+cudaError_t nalloc(amh_net* n, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) {
+    n->allocs.push_back((void*)*p);
+    e = cudaMemsetAsync(*p, 0, count * sizeof(T), n->stream);
+  }
+  return e;
+}
+#define NTRY(n, call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return nfail(n, e_ == cudaErrorMemoryAllocation ? AMH_ENOMEM : AMH_ECUDA, "%s: %s", #call, \
+                   cudaGetErrorString(e_));                                                    \
+  } while (0)
+
+int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* skip,
+         __nv_bfloat16* y16, __nv_bfloat16* r16, float* y32, int H, int W, int Cin, int Cout, int relu) {
+  ConvArgs a{x, w, bias, skip, y16, r16, y32, H, W, Cin, Cout, relu};
+  const size_t smem = (size_t)9 * 32 * (Cin + 8) * sizeof(__nv_bfloat16);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(conv3x3_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 32 * (128 + 8) * 2);
+    attr_set = true;
+  }
+  dim3 grid((W + 63) / 64, H, (Cout + 31) / 32);
+  conv3x3_fwd_kernel<<<grid, 128, smem, n->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
+  return AMH_OK;
+}
+void wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, int H, int W) {
+  const int Cin = kNet[L].cin, Cout = kNet[L].cout;
+  // enough blocks to fill the GPU a few times over; each strides over chunks
+  const int tiles = ((Cin + 31) / 32) * ((Cout + 31) / 32), nchunks = (H * W + kWgChunk - 1) / kWgChunk;
+  const int groups = std::max(1, std::min(nchunks, 4096 / (9 * tiles)));
+  dim3 grid((Cin + 31) / 32, (Cout + 31) / 32, 9 * groups);
+  conv3x3_wgrad_kernel<<<grid, 256, 0, n->stream>>>(x, dy, n->gw[L], n->gb[L], H, W, Cin, Cout);
+}
+// data gradient of layer L: dx (FP32, H x W x Cin) from dy (BF16 copy in g16)
+int dgrad(amh_net* n, int L, const __nv_bfloat16* dy16, float* dx, int H, int W) {
+  return conv(n, dy16, n->wd16[L], nullptr, nullptr, nullptr, nullptr, dx, H, W, kNet[L].cout, kNet[L].cin, 0);
+}
+}  // namespace
+
+extern "C" {
+
+AMH_API int amh_net_create(amh_net** out, int32_t width2, int32_t height2, uint64_t seed, void* stream) {
+  g_net_err.clear();
+  if (!out) return nfail(nullptr, AMH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (width2 < 8 || height2 < 8 || width2 % 8 || height2 % 8 || (size_t)width2 * height2 > (1u << 24))
+    return nfail(nullptr, AMH_EINVAL, "network size must be positive multiples of 8 (at most 2^24 pixels)");
+  amh_net* n = new (std::nothrow) amh_net();
+  if (!n) return nfail(nullptr, AMH_ENOMEM, "host allocation failed");
+  n->w2 = width2;
+  n->h2 = height2;
+  n->stream = (cudaStream_t)stream;
+  auto bail = [&](int code) {
+    g_net_err = n->err;
+    for (void* p : n->allocs) cudaFree(p);
+    delete n;
+    return code;
+  };
+#define NA(p, c)                                                  \
+  do {                                                            \
+    cudaError_t e_ = nalloc(n, &(p), (c));                        \
+    if (e_ != cudaSuccess) {                                      \
+      nfail(n, AMH_ENOMEM, "allocation: %s", cudaGetErrorString(e_)); \
+      return bail(AMH_ENOMEM);                                    \
+    }                                                             \
+  } while (0)
+  // He-normal initial weights from a seeded host generator (Box-Muller over
+  // a 64-bit LCG), zero biases
+  uint64_t s = seed * 6364136223846793005ull + 1442695040888963407ull;
+  auto uni = [&]() {
+    s = s * 6364136223846793005ull + 1442695040888963407ull;
+    return ((s >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (int L = 0; L < kLayers; L++) {
+    const int Cin = kNet[L].cin, Cout = kNet[L].cout;
+    const size_t nw = (size_t)9 * Cin * Cout;
+    NA(n->wm[L], nw); NA(n->w16[L], nw); NA(n->wd16[L], nw); NA(n->mw[L], nw); NA(n->vw[L], nw); NA(n->gw[L], nw);
+    NA(n->bm[L], Cout); NA(n->mb[L], Cout); NA(n->vb[L], Cout); NA(n->gb[L], Cout);
+    std::vector<float> w(nw);
+    const double sd = std::sqrt(2.0 / (9.0 * Cin)) * (L == kLayers - 1 ? 0.1 : 1.0);
+    for (size_t i = 0; i < nw; i++) w[i] = (float)(sd * std::sqrt(-2.0 * std::log(uni())) * std::cos(6.283185307179586 * uni()));
+    cudaMemcpyAsync(n->wm[L], w.data(), nw * sizeof(float), cudaMemcpyHostToDevice, n->stream);
+    cudaStreamSynchronize(n->stream);
+  }
+  const size_t P0 = (size_t)width2 * height2, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  NA(n->x0, P0 * 16); NA(n->e1, P0 * 32); NA(n->in_e2, P1 * 32); NA(n->e2, P1 * 64); NA(n->in_e3, P2 * 64);
+  NA(n->e3, P2 * 96); NA(n->in_e4, P3 * 96); NA(n->e4, P3 * 128); NA(n->in_d3, P2 * 128); NA(n->r3, P2 * 96);
+  NA(n->d3, P2 * 96); NA(n->in_d2, P1 * 96); NA(n->r2, P1 * 64); NA(n->d2, P1 * 64); NA(n->in_d1, P0 * 64);
+  NA(n->r1, P0 * 32); NA(n->d1, P0 * 32);
+  n->maxel = P0 * 64;
+  NA(n->g16, n->maxel); NA(n->gA, n->maxel); NA(n->gB, n->maxel);
+  {
+    const size_t lp[kLayers] = {P0, P1, P2, P3, P2, P1, P0, P0};   // output size of each layer
+    for (int L = 0; L < kLayers; L++) NA(n->dy[L], lp[L] * kNet[L].cout);
+  }
+  NA(n->gE1, P0 * 32); NA(n->gE2, P1 * 64); NA(n->gE3, P2 * 96);
+  NA(n->out, P0 * 16); NA(n->target, P0 * 4); NA(n->mask, P0); NA(n->pin, P0); NA(n->prop, P0); NA(n->loss, 1);
+#undef NA
+  for (int L = 0; L < kLayers; L++) {
+    const size_t nw = (size_t)9 * kNet[L].cin * kNet[L].cout;
+    to_bf16_kernel<<<blocks_for(nw), 256, 0, n->stream>>>(n->wm[L], n->w16[L], nw);
+    flip_transpose_kernel<<<blocks_for(nw), 256, 0, n->stream>>>(n->w16[L], n->wd16[L], kNet[L].cin, kNet[L].cout);
+  }
+  cudaError_t e = cudaStreamSynchronize(n->stream);
+  if (e != cudaSuccess) {
+    nfail(n, AMH_ECUDA, "net init: %s", cudaGetErrorString(e));
+    return bail(AMH_ECUDA);
+  }
+  *out = n;
+  return AMH_OK;
+}
+
+AMH_API int amh_net_params(amh_net* n, int32_t layer, float* w, float* b, int32_t set) {
+  if (!n || layer < 0 || layer >= kLayers) return AMH_EINVAL;
+  const size_t nw = (size_t)9 * kNet[layer].cin * kNet[layer].cout, nb = kNet[layer].cout;
+  if (set) {
+    if (w) NTRY(n, cudaMemcpyAsync(n->wm[layer], w, nw * 4, cudaMemcpyHostToDevice, n->stream));
+    if (b) NTRY(n, cudaMemcpyAsync(n->bm[layer], b, nb * 4, cudaMemcpyHostToDevice, n->stream));
+    to_bf16_kernel<<<blocks_for(nw), 256, 0, n->stream>>>(n->wm[layer], n->w16[layer], nw);
+    flip_transpose_kernel<<<blocks_for(nw), 256, 0, n->stream>>>(n->w16[layer], n->wd16[layer], kNet[layer].cin,
+                                                                kNet[layer].cout);
+  } else {
+    if (w) NTRY(n, cudaMemcpyAsync(w, n->wm[layer], nw * 4, cudaMemcpyDeviceToHost, n->stream));
+    if (b) NTRY(n, cudaMemcpyAsync(b, n->bm[layer], nb * 4, cudaMemcpyDeviceToHost, n->stream));
+  }
+  NTRY(n, cudaStreamSynchronize(n->stream));
+  return AMH_OK;
+}
+
+AMH_API int amh_net_grads(amh_net* n, int32_t layer, float* gw, float* gb) {
+  if (!n || layer < 0 || layer >= kLayers) return AMH_EINVAL;
+  const size_t nw = (size_t)9 * kNet[layer].cin * kNet[layer].cout, nb = kNet[layer].cout;
+  if (gw) NTRY(n, cudaMemcpyAsync(gw, n->gw[layer], nw * 4, cudaMemcpyDeviceToHost, n->stream));
+  if (gb) NTRY(n, cudaMemcpyAsync(gb, n->gb[layer], nb * 4, cudaMemcpyDeviceToHost, n->stream));
+  NTRY(n, cudaStreamSynchronize(n->stream));
+  return AMH_OK;
+}
+
+// input features (H2 x W2 x 16) from the host (tests), or from a context
+AMH_API int amh_net_set_input(amh_net* n, const float* x0_host) {
+  if (!n || !x0_host) return AMH_EINVAL;
+  const size_t ne = (size_t)n->w2 * n->h2 * 16;
+  std::vector<__nv_bfloat16> h(ne);
+  for (size_t i = 0; i < ne; i++) h[i] = __float2bfloat16(x0_host[i]);
+  NTRY(n, cudaMemcpyAsync(n->x0, h.data(), ne * 2, cudaMemcpyHostToDevice, n->stream));
+  NTRY(n, cudaStreamSynchronize(n->stream));
+  return AMH_OK;
+}
+
+AMH_API int amh_net_features(amh_net* n, amh_ctx* c) {
+  if (!n || !c) return AMH_EINVAL;
+  if ((c->W + 1) / 2 > n->w2 || (c->H + 1) / 2 > n->h2) return nfail(n, AMH_EINVAL, "context larger than the network");
+  const float lmid = 0.5f * (std::log(c->p.depth_min) + std::log(c->p.depth_max));
+  const float lscale = 2.f / std::max(1e-6f, std::log(c->p.depth_max / c->p.depth_min));
+  NTRY(n, cudaMemsetAsync(n->x0, 0, (size_t)n->w2 * n->h2 * 16 * 2, n->stream));
+  features_kernel<<<blocks_for((size_t)n->w2 * n->h2), 256, 0, n->stream>>>(
+      c->d_ref, c->args.img_half, c->d_plane, c->d_cost, c->W, c->H, n->w2, n->h2, lmid, lscale, n->x0, n->pin);
+  NTRY(n, cudaGetLastError());
+  return AMH_OK;
+}
+
+AMH_API int amh_net_targets(amh_net* n, amh_ctx* c, float cost_max) {
+  if (!n || !c) return AMH_EINVAL;
+  targets_kernel<<<blocks_for((size_t)n->w2 * n->h2), 256, 0, n->stream>>>(
+      c->d_plane, c->d_cost, n->pin, c->W, c->H, n->w2, n->h2, cost_max, n->target, n->mask);
+  NTRY(n, cudaGetLastError());
+  return AMH_OK;
+}
+
+AMH_API int amh_net_set_targets(amh_net* n, const float* target_host, const uint8_t* mask_host) {
+  if (!n || !target_host || !mask_host) return AMH_EINVAL;
+  const size_t np = (size_t)n->w2 * n->h2;
+  NTRY(n, cudaMemcpyAsync(n->target, target_host, np * 16, cudaMemcpyHostToDevice, n->stream));
+  NTRY(n, cudaMemcpyAsync(n->mask, mask_host, np, cudaMemcpyHostToDevice, n->stream));
+  NTRY(n, cudaStreamSynchronize(n->stream));
+  return AMH_OK;
+}
+
+AMH_API int amh_net_forward(amh_net* n, float* out_host) {
+  if (!n) return AMH_EINVAL;
+  const int W0 = n->w2, H0 = n->h2, W1 = W0 / 2, H1 = H0 / 2, W2 = W1 / 2, H2 = H1 / 2, W3 = W2 / 2, H3 = H2 / 2;
+  const cudaStream_t s = n->stream;
+  int rc = conv(n, n->x0, n->w16[0], n->bm[0], nullptr, n->e1, nullptr, nullptr, H0, W0, 16, 32, 1);
+  pool2_kernel<<<blocks_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->e1, n->in_e2, H0, W0, 32);
+  if (!rc) rc = conv(n, n->in_e2, n->w16[1], n->bm[1], nullptr, n->e2, nullptr, nullptr, H1, W1, 32, 64, 1);
+  pool2_kernel<<<blocks_for((size_t)H2 * W2 * 64), 256, 0, s>>>(n->e2, n->in_e3, H1, W1, 64);
+  if (!rc) rc = conv(n, n->in_e3, n->w16[2], n->bm[2], nullptr, n->e3, nullptr, nullptr, H2, W2, 64, 96, 1);
+  pool2_kernel<<<blocks_for((size_t)H3 * W3 * 96), 256, 0, s>>>(n->e3, n->in_e4, H2, W2, 96);
+  if (!rc) rc = conv(n, n->in_e4, n->w16[3], n->bm[3], nullptr, n->e4, nullptr, nullptr, H3, W3, 96, 128, 1);
+  up2_kernel<<<blocks_for((size_t)H2 * W2 * 128), 256, 0, s>>>(n->e4, n->in_d3, H2, W2, 128);
+  if (!rc) rc = conv(n, n->in_d3, n->w16[4], n->bm[4], n->e3, n->d3, n->r3, nullptr, H2, W2, 128, 96, 1);
+  up2_kernel<<<blocks_for((size_t)H1 * W1 * 96), 256, 0, s>>>(n->d3, n->in_d2, H1, W1, 96);
+  if (!rc) rc = conv(n, n->in_d2, n->w16[5], n->bm[5], n->e2, n->d2, n->r2, nullptr, H1, W1, 96, 64, 1);
+  up2_kernel<<<blocks_for((size_t)H0 * W0 * 64), 256, 0, s>>>(n->d2, n->in_d1, H0, W0, 64);
+  if (!rc) rc = conv(n, n->in_d1, n->w16[6], n->bm[6], n->e1, n->d1, n->r1, nullptr, H0, W0, 64, 32, 1);
+  if (!rc) rc = conv(n, n->d1, n->w16[7], n->bm[7], nullptr, nullptr, nullptr, n->out, H0, W0, 32, 16, 0);
+  if (rc) return rc;
+  NTRY(n, cudaGetLastError());
+  if (out_host) {
+    NTRY(n, cudaMemcpyAsync(out_host, n->out, (size_t)H0 * W0 * 16 * 4, cudaMemcpyDeviceToHost, s));
+    NTRY(n, cudaStreamSynchronize(s));
+  }
+  return AMH_OK;
+}
+
+// loss of the last forward against the targets, and all gradients
+AMH_API int amh_net_backward(amh_net* n, float* loss_out) {
+  if (!n) return AMH_EINVAL;
+  const int W0 = n->w2, H0 = n->h2, W1 = W0 / 2, H1 = H0 / 2, W2 = W1 / 2, H2 = H1 / 2, W3 = W2 / 2, H3 = H2 / 2;
+  const size_t P0 = (size_t)W0 * H0, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  const cudaStream_t s = n->stream;
+  // mask count on the host side of the stream
+  std::vector<uint8_t> mk(P0);
+  NTRY(n, cudaMemcpyAsync(mk.data(), n->mask, P0, cudaMemcpyDeviceToHost, s));
+  NTRY(n, cudaStreamSynchronize(s));
+  size_t cnt = 0;
+  for (uint8_t m : mk) cnt += m;
+  const float inv_n = 1.f / (float)std::max<size_t>(1, cnt);
+  for (int L = 0; L < kLayers; L++) {
+    NTRY(n, cudaMemsetAsync(n->gw[L], 0, (size_t)9 * kNet[L].cin * kNet[L].cout * 4, s));
+    NTRY(n, cudaMemsetAsync(n->gb[L], 0, (size_t)kNet[L].cout * 4, s));
+  }
+  NTRY(n, cudaMemsetAsync(n->loss, 0, 4, s));
+  float* const* dy = n->dy;
+  l1_loss_kernel<<<blocks_for(P0), 256, 0, s>>>(n->out, n->target, n->mask, dy[7], n->loss, (int)P0, inv_n);
+  // out = conv(d1)
+  wgrad(n, 7, n->d1, dy[7], H0, W0);
+  to_bf16_kernel<<<blocks_for(P0 * 16), 256, 0, s>>>(dy[7], n->g16, P0 * 16);
+  int rc = dgrad(n, 7, n->g16, n->gA, H0, W0);                       // gA = d d1 (P0 x 32)
+  // d1 = relu(conv(in_d1)) + e1
+  NTRY(n, cudaMemcpyAsync(n->gE1, n->gA, P0 * 32 * 4, cudaMemcpyDeviceToDevice, s));
+  relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gA, n->r1, dy[6], n->g16, P0 * 32);
+  wgrad(n, 6, n->in_d1, dy[6], H0, W0);
+  if (!rc) rc = dgrad(n, 6, n->g16, n->gA, H0, W0);                  // d in_d1 (P0 x 64)
+  up2_bwd_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gA, n->gE2, H1, W1, 64);  // d d2 (P1 x 64)
+  relu_mask_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gE2, n->r2, dy[5], n->g16, P1 * 64);
+  wgrad(n, 5, n->in_d2, dy[5], H1, W1);
+  if (!rc) rc = dgrad(n, 5, n->g16, n->gA, H1, W1);                  // d in_d2 (P1 x 96)
+  up2_bwd_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gA, n->gE3, H2, W2, 96);  // d d3 (P2 x 96)
+  relu_mask_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gE3, n->r3, dy[4], n->g16, P2 * 96);
+  wgrad(n, 4, n->in_d3, dy[4], H2, W2);
+  if (!rc) rc = dgrad(n, 4, n->g16, n->gA, H2, W2);                  // d in_d3 (P2 x 128)
+  up2_bwd_kernel<<<blocks_for(P3 * 128), 256, 0, s>>>(n->gA, n->gB, H3, W3, 128); // d e4 (P3 x 128)
+  // e4 = relu(conv(in_e4))
+  relu_mask_kernel<<<blocks_for(P3 * 128), 256, 0, s>>>(n->gB, n->e4, dy[3], n->g16, P3 * 128);
+  wgrad(n, 3, n->in_e4, dy[3], H3, W3);
+  if (!rc) rc = dgrad(n, 3, n->g16, n->gA, H3, W3);                  // d in_e4 (P3 x 96)
+  pool2_bwd_add_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gA, n->gE3, H2, W2, 96);
+  // e3 = relu(conv(in_e3)), read by d3 (skip) and by the pooling
+  relu_mask_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gE3, n->e3, dy[2], n->g16, P2 * 96);
+  wgrad(n, 2, n->in_e3, dy[2], H2, W2);
+  if (!rc) rc = dgrad(n, 2, n->g16, n->gA, H2, W2);                  // d in_e3 (P2 x 64)
+  pool2_bwd_add_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gA, n->gE2, H1, W1, 64);
+  relu_mask_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gE2, n->e2, dy[1], n->g16, P1 * 64);
+  wgrad(n, 1, n->in_e2, dy[1], H1, W1);
+  if (!rc) rc = dgrad(n, 1, n->g16, n->gA, H1, W1);                  // d in_e2 (P1 x 32)
+  pool2_bwd_add_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gA, n->gE1, H0, W0, 32);
+  relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gE1, n->e1, dy[0], nullptr, P0 * 32);
+  wgrad(n, 0, n->x0, dy[0], H0, W0);
+  if (rc) return rc;
+  NTRY(n, cudaGetLastError());
+  if (loss_out) {
+    NTRY(n, cudaMemcpyAsync(loss_out, n->loss, 4, cudaMemcpyDeviceToHost, s));
+    NTRY(n, cudaStreamSynchronize(s));
+  }
+  return AMH_OK;
+}
+
+AMH_API int amh_net_adam(amh_net* n, float lr) {
+  if (!n) return AMH_EINVAL;
+  n->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
+  for (int L = 0; L < kLayers; L++) {
+    const size_t nw = (size_t)9 * kNet[L].cin * kNet[L].cout;
+    adam_kernel<<<blocks_for(nw), 256, 0, n->stream>>>(n->wm[L], n->mw[L], n->vw[L], n->gw[L], n->w16[L], (int)nw,
+                                                     lr, b1, b2, 1e-8f, c1, c2);
+    adam_kernel<<<1, 256, 0, n->stream>>>(n->bm[L], n->mb[L], n->vb[L], n->gb[L], nullptr, kNet[L].cout, lr, b1, b2,
+                                         1e-8f, c1, c2);
+    flip_transpose_kernel<<<blocks_for(nw), 256, 0, n->stream>>>(n->w16[L], n->wd16[L], kNet[L].cin, kNet[L].cout);
+  }
+  NTRY(n, cudaGetLastError());
+  return AMH_OK;
+}
+
+// the proposal planes of the last forward, handed to the context's phases
+AMH_API int amh_net_propose(amh_net* n, amh_ctx* c) {
+  if (!n || !c) return AMH_EINVAL;
+  head_kernel<<<blocks_for((size_t)n->w2 * n->h2), 256, 0, n->stream>>>(n->out, n->pin, c->W, c->H, n->w2, n->h2,
+                                                                        c->args, n->prop);
+  NTRY(n, cudaGetLastError());
+  c->args.prop = n->prop;
+  c->args.prop_w = n->w2;
+  c->args.prop_h = n->h2;
+  return AMH_OK;
+}
+
+AMH_API int amh_clear_proposal(amh_ctx* c) {
+  if (!c) return AMH_EINVAL;
+  c->args.prop = nullptr;
+  return AMH_OK;
+}
+
+// internal tensors for element-wise checks of every operation
+AMH_API int amh_net_read(amh_net* n, int32_t which, float* out, int64_t* count) {
+  if (!n || !count) return AMH_EINVAL;
+  const size_t P0 = (size_t)n->w2 * n->h2, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  struct B { const __nv_bfloat16* b; const float* f; size_t n; };
+  const B act[] = {{n->x0, nullptr, P0 * 16},   {n->e1, nullptr, P0 * 32},    {n->in_e2, nullptr, P1 * 32},
+                   {n->e2, nullptr, P1 * 64},   {n->in_e3, nullptr, P2 * 64}, {n->e3, nullptr, P2 * 96},
+                   {n->in_e4, nullptr, P3 * 96}, {n->e4, nullptr, P3 * 128},  {n->in_d3, nullptr, P2 * 128},
+                   {n->r3, nullptr, P2 * 96},   {n->d3, nullptr, P2 * 96},    {n->in_d2, nullptr, P1 * 96},
+                   {n->r2, nullptr, P1 * 64},   {n->d2, nullptr, P1 * 64},    {n->in_d1, nullptr, P0 * 64},
+                   {n->r1, nullptr, P0 * 32},   {n->d1, nullptr, P0 * 32},    {nullptr, n->out, P0 * 16}};
+  constexpr int kAct = (int)(sizeof(act) / sizeof(act[0]));
+  const size_t lp[kLayers] = {P0, P1, P2, P3, P2, P1, P0, P0};
+  B src{};
+  if (which >= 0 && which < kAct) src = act[which];
+  else if (which >= 32 && which < 32 + kLayers) src = B{nullptr, n->dy[which - 32], lp[which - 32] * kNet[which - 32].cout};
+  else return nfail(n, AMH_EINVAL, "unknown tensor %d", which);
+  if (!out) {
+    *count = (int64_t)src.n;
+    return AMH_OK;
+  }
+  if (*count != (int64_t)src.n) return nfail(n, AMH_EINVAL, "tensor %d has %zu elements, not %lld", which, src.n, (long long)*count);
+  const float* dev = src.f;
+  if (src.b) {   // BF16 -> FP32 in the scratch buffer (the largest tensor fits)
+    bf16_to_f32_kernel<<<blocks_for(src.n), 256, 0, n->stream>>>(src.b, n->gB, src.n);
+    NTRY(n, cudaGetLastError());
+    dev = n->gB;
+  }
+  NTRY(n, cudaMemcpyAsync(out, dev, src.n * 4, cudaMemcpyDeviceToHost, n->stream));
+  NTRY(n, cudaStreamSynchronize(n->stream));
+  return AMH_OK;
+}
+
+AMH_API int amh_net_synchronize(amh_net* n) {
+  if (!n) return AMH_EINVAL;
+  NTRY(n, cudaStreamSynchronize(n->stream));
+  return AMH_OK;
+}
+
+AMH_API const char* amh_net_last_error(const amh_net* n) { return n ? n->err.c_str() : g_net_err.c_str(); }
+
+AMH_API void amh_net_destroy(amh_net* n) {
+  if (!n) return;
+  cudaStreamSynchronize(n->stream);
+  for (void* p : n->allocs) cudaFree(p);
+  delete n;
+}
+
+}  // extern "C"

@@ -400,12 +400,24 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   }
 
   // --- Sec. 3.3: refinement with the same weights -------------------------------------
+  // A learned proposal (n, d) of this pixel's 2 x 2 block, when present, is one
+  // more candidate after the refinement ones, judged by the same weights.
   const int nc = a.t < 3 ? 1 : kMaxRefine;
+  float4 prop = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool has_prop = false;
+  if (a.prop) {
+    const float4 pr = a.prop[(size_t)min(y / 2, a.prop_h - 1) * a.prop_w + min(x / 2, a.prop_w - 1)];
+    const float den = pr.x * ray.x + pr.y * ray.y + pr.z * ray.z;
+    const float Dx = den < 0.f ? -pr.w / den : 0.f;
+    has_prop = pr.w > 0.f && Dx > 0.f && isfinite(Dx);
+    prop = make_float4(pr.x, pr.y, pr.z, Dx);
+  }
+  const int ncand = nc + (has_prop ? 1 : 0);
   int bc = -1;
   float bcm = 0.f;
 #pragma unroll 1
-  for (int ci = 0; ci < nc; ci++) {
-    ok = plane_c(a.Kinv, refine_candidate(a, x, y, best, ray, ci), ray, &c);
+  for (int ci = 0; ci < ncand; ci++) {
+    ok = plane_c(a.Kinv, ci < nc ? refine_candidate(a, x, y, best, ray, ci) : prop, ray, &c);
     float m = 0.f;
     for (int j = 0; j < N; j++) {
       const float wj = sm.wt(j);
@@ -416,8 +428,8 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   }
   if (bc >= 0 && bcm < bm) {
     bm = bcm;
-    best = refine_candidate(a, x, y, best, ray, bc);
-    choice = 9 + bc;
+    best = bc < nc ? refine_candidate(a, x, y, best, ray, bc) : prop;
+    choice = bc < nc ? 9 + bc : 15;
   }
   a.plane[pi] = best;
   a.cost[pi] = bm;

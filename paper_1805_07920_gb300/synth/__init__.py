@@ -305,7 +305,7 @@ def ring_sources(ref, n=20, n_src=10):
 
 
 SCENES = {"tiny": scene_tiny, "medium": scene_medium, "large": scene_large,
-          "ring20": scene_ring20}
+          "ring20": scene_ring20, "learned": scene_learned}
 
 
 def make_scene(name: str, seed: int | None = None, cache_dir: str | None = None) -> Scene:
