@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-form and learned-proposal measurements")
     return ap.parse_args()
 
 
@@ -322,6 +323,8 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras["batched_ring20"] = bench_batch(args, dist)
+        if rank == 0:
+            extras["learned_proposal_1600x1056"] = bench_learned()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -385,6 +388,30 @@ def bench_batch(args, dist):
             "pixels_per_iteration": px, "pairs_per_batch": pairs, "launches_per_batch": 1 + 2 * ITERS,
             "tile_variant": ["16x16", "32x8", "64x4"][chosen],
             "autotune_ms": [round(float(m), 3) for m in tune_ms], "timing": "host wall clock around graph launches"}
+
+
+def bench_learned():
+    """Learned-proposal form on a held-out 1600x1056 scene with 10 sources:
+    device time of the plain method's init + 6 iterations against the time
+    the proposal schedule (network on the state after 2 iterations) needs to
+    reach the same accuracy (pixels within 1 % of the ground-truth depth)."""
+    from paper_1805_07920_gb300 import amh, learned, synth
+    seed = 2003
+    sc = synth.make_scene("learned", seed=seed)
+    w2, h2 = amh.net_size_for(sc.width, sc.height)
+    net = amh.Net(w2, h2)
+    net.load(learned.WEIGHTS)
+    r = learned.evaluate_scene(sc, net, seed, schedules={"net@2": learned.SCHEDULES["net@2"]}, log=lambda s: None)
+    s = r["schedules"]["net@2"]
+    net.close()
+    return {"scene": f"learned seed {seed}: {sc.width}x{sc.height}, {len(sc.src)} sources",
+            "plain_ms_6_iterations": round(r["ms_plain_final"], 3), "plain_accuracy_1pct": round(r["acc_plain"][-1], 4),
+            "learned_iterations_to_plain_accuracy": s["iters_to_plain_final"],
+            "learned_ms_to_plain_accuracy": None if s["ms_to_plain_final"] is None else round(s["ms_to_plain_final"], 3),
+            "network_ms": [round(m, 3) for m in s["ms_net"]],
+            "accuracy_per_iteration": {"plain": [round(a, 4) for a in r["acc_plain"]],
+                                       "learned": [round(a, 4) for a in s["acc"]]},
+            "timing": "CUDA events per iteration on the launching stream (accuracy read-back excluded)"}
 
 
 def main():
