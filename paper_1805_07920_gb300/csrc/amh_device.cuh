@@ -80,6 +80,49 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 __device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
 // hardware reciprocal (MUFU), about 1 ulp
+// Two FP32 lanes in one 64-bit register pair, for the packed f32x2
+// arithmetic of sm_100-class SMs (one instruction issues both lanes; each lane
+// rounds exactly as the scalar instruction would).
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 pack2(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f2 p, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p.v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+// floor of both lanes for |x| < 2^22: x + 2^23 rounded towards -inf is
+// 2^23 + floor(x) exactly (the spacing there is 1), and removing 2^23 is exact
+__device__ __forceinline__ f2 floor2(f2 x) {
+  const f2 M = pack2(8388608.f, 8388608.f);
+  f2 t;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(t.v) : "l"(x.v), "l"(M.v));
+  return sub2(t, M);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -51,11 +51,13 @@ static_assert(acp_dx(71) == 23 && acp_dy(71) == 0, "far right ends at (23, 0)");
 // {-5,-3,-1,1,3,5}^2 clamped to the image; w = exp(-|I - I_c| / (2 sigma_I^2)
 // - |dx| / (2 sigma_x^2)); the values centred on their weighted mean so that
 // cov(r, s) = sum w r^ s / sum w.
+// Stored as lane pairs (samples 2m, 2m + 1) for the packed moment updates.
 struct RefWin {
-  float w[kWinS];
-  float wr[kWinS];
+  f2 w2[kWinS / 2];
+  f2 wr2[kWinS / 2];
   float inv_sw, sum_wr, var_r;
 };
+static_assert(kWinS % 2 == 0 && kWinN % 2 == 0, "window samples are processed in pairs along a row");
 
 // intensity of reference pixel i (uint8 or FP16 images)
 template <bool kHalf, class A>
@@ -71,7 +73,7 @@ __host__ __device__ constexpr float tex_scale() { return kHalf ? 1.f : 255.f; }
 template <bool kHalf, class A>
 __device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin& rw) {
   const float Ic = ref_at<kHalf, A>(a, (size_t)y * a.W + x);
-  float rv[kWinS];
+  float rv[kWinS], wv[kWinS];
   float sw = 0.f, s1 = 0.f;
 #pragma unroll
   for (int k = 0; k < kWinS; k++) {
@@ -82,20 +84,25 @@ __device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin
     if (a.squared) { dI = r * r; dx = (float)(du * du + dv * dv); }
     const float w = expf(-dI * a.wI - dx * a.wX);
     rv[k] = r;
-    rw.w[k] = w;
+    wv[k] = w;
     sw += w;
     s1 = fmaf(w, r, s1);
   }
   const float inv = 1.f / sw;
   const float mr = s1 * inv;
-  float s2 = 0.f, swr = 0.f;
+  float s2 = 0.f, swr = 0.f, wrv[kWinS];
 #pragma unroll
   for (int k = 0; k < kWinS; k++) {
     const float rc = rv[k] - mr;
-    const float wr = rw.w[k] * rc;
-    rw.wr[k] = wr;
+    const float wr = wv[k] * rc;
+    wrv[k] = wr;
     swr += wr;
     s2 = fmaf(wr, rc, s2);
+  }
+#pragma unroll
+  for (int m = 0; m < kWinS / 2; m++) {
+    rw.w2[m] = pack2(wv[2 * m], wv[2 * m + 1]);
+    rw.wr2[m] = pack2(wrv[2 * m], wrv[2 * m + 1]);
   }
   rw.inv_sw = inv;
   rw.sum_wr = swr;
@@ -129,33 +136,57 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
   const float sx0 = fmaf(-R, H0 + H1, px), sy0 = fmaf(-R, H3 + H4, py), sz0 = fmaf(-R, H6 + H7, pz);
   const float cxs = St * H0, cys = St * H3, czs = St * H6;
   const float rxs = St * H1, rys = St * H4, rzs = St * H7;
-  float s0 = 0.f, m1 = 0.f, m2 = 0.f, mrs = 0.f;
-#pragma unroll
+  // Samples (cb, cb + 1) of a row share one lane pair: sample position,
+  // projective division, floor / fraction and the three moments run as packed
+  // f32x2 operations; the gathers and the bilinear blends are per sample.
+  const f2 cx2 = pack2(cxs, cxs), cy2 = pack2(cys, cys), cz2 = pack2(czs, czs);
+  f2 acc1 = pack2(0.f, 0.f), acc2 = pack2(0.f, 0.f), accr = pack2(0.f, 0.f);
+  f2 s0p = pack2(0.f, 0.f);
+#pragma unroll 1   // rows stay a loop: smaller code; the weights come from L1
   for (int ra = 0; ra < kWinN; ra++) {
     const float bx = fmaf((float)ra, rxs, sx0), by = fmaf((float)ra, rys, sy0), bz = fmaf((float)ra, rzs, sz0);
+    const f2 bx2 = pack2(bx, bx), by2 = pack2(by, by), bz2 = pack2(bz, bz);
 #pragma unroll
-    for (int cb = 0; cb < kWinN; cb++) {
-      const int k = ra * kWinN + cb;
-      const float qx = fmaf((float)cb, cxs, bx), qy = fmaf((float)cb, cys, by), qz = fmaf((float)cb, czs, bz);
-      const float iq = rcp_approx(qz);
-      const float gx = qx * iq, gy = qy * iq;
-      const float fx0 = floorf(gx), fy0 = floorf(gy);
-      const float fx = gx - fx0, fy = gy - fy0;
+    for (int cb = 0; cb < kWinN; cb += 2) {
+      const int m = (ra * kWinN + cb) / 2;
+      const f2 cc = pack2((float)cb, (float)(cb + 1));
+      const f2 qx = fma2(cc, cx2, bx2), qy = fma2(cc, cy2, by2), qz = fma2(cc, cz2, bz2);
+      float qz0, qz1;
+      unpack2(qz, qz0, qz1);
+      const f2 iq = pack2(rcp_approx(qz0), rcp_approx(qz1));
+      const f2 gx = mul2(qx, iq), gy = mul2(qy, iq);
+      const f2 flx = floor2(gx), fly = floor2(gy);
+      const f2 frx = sub2(gx, flx), fry = sub2(gy, fly);
+      float x0a, x0b, y0a, y0b, fxa, fxb, fya, fyb;
+      unpack2(flx, x0a, x0b);
+      unpack2(fly, y0a, y0b);
+      unpack2(frx, fxa, fxb);
+      unpack2(fry, fya, fyb);
       // texels: w (x0, y0), z (x0+1, y0), x (x0, y0+1), y (x0+1, y0+1)
-      const float4 g = tex2Dgather<float4>(V.tex, fx0, fy0, 0);
-      const float top = fmaf(fx, g.z - g.w, g.w);
-      const float bot = fmaf(fx, g.y - g.x, g.x);
-      const float s = fmaf(fy, bot - top, top);
+      const float4 ga = tex2Dgather<float4>(V.tex, x0a, y0a, 0);
+      const float4 gb = tex2Dgather<float4>(V.tex, x0b, y0b, 0);
+      const float ta = fmaf(fxa, ga.z - ga.w, ga.w), ba = fmaf(fxa, ga.y - ga.x, ga.x);
+      const float tb = fmaf(fxb, gb.z - gb.w, gb.w), bb = fmaf(fxb, gb.y - gb.x, gb.x);
+      const f2 sp = pack2(fmaf(fya, ba - ta, ta), fmaf(fyb, bb - tb, tb));
       // moments about the first sample: exact zero variance for constant
       // patches in FP32
-      if (k == 0) s0 = s;
-      const float sc = s - s0;
-      const float ws = rw.w[k] * sc;
-      m1 += ws;
-      m2 = fmaf(ws, sc, m2);
-      mrs = fmaf(rw.wr[k], sc, mrs);
+      if (m == 0) {
+        float s0, s1_;
+        unpack2(sp, s0, s1_);
+        s0p = pack2(s0, s0);
+      }
+      const f2 sc = sub2(sp, s0p);
+      const f2 ws = mul2(rw.w2[m], sc);
+      acc1 = add2(acc1, ws);
+      acc2 = fma2(ws, sc, acc2);
+      accr = fma2(rw.wr2[m], sc, accr);
     }
   }
+  float m1a, m1b, m2a, m2b, mra, mrb;
+  unpack2(acc1, m1a, m1b);
+  unpack2(acc2, m2a, m2b);
+  unpack2(accr, mra, mrb);
+  const float m1 = m1a + m1b, m2 = m2a + m2b, mrs = mra + mrb;
   const float es = m1 * rw.inv_sw;
   const float var_s = fmaf(m2, rw.inv_sw, -es * es);
   const float cov = fmaf(mrs, rw.inv_sw, -(rw.sum_wr * rw.inv_sw) * es);
