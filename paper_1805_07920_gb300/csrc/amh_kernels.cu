@@ -13,7 +13,7 @@ using namespace upd;
 
 constexpr int kTile = 16;
 constexpr int kThreads = 128;
-constexpr int kPhaseBlocksPerSM = 4;          // 128 registers per thread
+constexpr int kPhaseBlocksPerSM = 3;          // 168 registers per thread
 
 __device__ __forceinline__ void count_pairs(const PhaseArgs& a, int npairs) {
   const int tot = __reduce_add_sync(0xffffffffu, npairs);

@@ -136,32 +136,37 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
   const float sx0 = fmaf(-R, H0 + H1, px), sy0 = fmaf(-R, H3 + H4, py), sz0 = fmaf(-R, H6 + H7, pz);
   const float cxs = St * H0, cys = St * H3, czs = St * H6;
   const float rxs = St * H1, rys = St * H4, rzs = St * H7;
-  // Samples (cb, cb + 1) of a row share one lane pair: sample position,
-  // projective division, floor / fraction and the three moments run as packed
-  // f32x2 operations; the gathers and the bilinear blends are per sample.
-  const f2 cx2 = pack2(cxs, cxs), cy2 = pack2(cys, cys), cz2 = pack2(czs, czs);
+  // Packed f32x2 arithmetic: the (x, y) position, floor and fraction of each
+  // sample form one lane pair (the gather takes them as a pair), the depths
+  // and the three moments of samples (cb, cb + 1) of a row another; the
+  // gathers and the bilinear blends are per sample.
+  const f2 cxy = pack2(cxs, cys), cz2 = pack2(czs, czs);
   f2 acc1 = pack2(0.f, 0.f), acc2 = pack2(0.f, 0.f), accr = pack2(0.f, 0.f);
   f2 s0p = pack2(0.f, 0.f);
-#pragma unroll 1   // rows stay a loop: smaller code; the weights come from L1
+#pragma unroll
   for (int ra = 0; ra < kWinN; ra++) {
     const float bx = fmaf((float)ra, rxs, sx0), by = fmaf((float)ra, rys, sy0), bz = fmaf((float)ra, rzs, sz0);
-    const f2 bx2 = pack2(bx, bx), by2 = pack2(by, by), bz2 = pack2(bz, bz);
+    const f2 bxy = pack2(bx, by), bz2 = pack2(bz, bz);
 #pragma unroll
     for (int cb = 0; cb < kWinN; cb += 2) {
       const int m = (ra * kWinN + cb) / 2;
-      const f2 cc = pack2((float)cb, (float)(cb + 1));
-      const f2 qx = fma2(cc, cx2, bx2), qy = fma2(cc, cy2, by2), qz = fma2(cc, cz2, bz2);
-      float qz0, qz1;
+      // (x, y) of each sample in one lane pair (the gather takes them as a pair)
+      const f2 qa = fma2(pack2((float)cb, (float)cb), cxy, bxy);
+      const f2 qb = fma2(pack2((float)(cb + 1), (float)(cb + 1)), cxy, bxy);
+      const f2 qz = fma2(pack2((float)cb, (float)(cb + 1)), cz2, bz2);
+      float qz0, qz1, qxa, qya, qxb, qyb;
       unpack2(qz, qz0, qz1);
-      const f2 iq = pack2(rcp_approx(qz0), rcp_approx(qz1));
-      const f2 gx = mul2(qx, iq), gy = mul2(qy, iq);
-      const f2 flx = floor2(gx), fly = floor2(gy);
-      const f2 frx = sub2(gx, flx), fry = sub2(gy, fly);
+      unpack2(qa, qxa, qya);
+      unpack2(qb, qxb, qyb);
+      const float ia = rcp_approx(qz0), ib = rcp_approx(qz1);
+      const f2 pa = pack2(qxa * ia, qya * ia), pb = pack2(qxb * ib, qyb * ib);
+      const f2 fla = floor2(pa), flb = floor2(pb);
+      const f2 fra = sub2(pa, fla), frb = sub2(pb, flb);
       float x0a, x0b, y0a, y0b, fxa, fxb, fya, fyb;
-      unpack2(flx, x0a, x0b);
-      unpack2(fly, y0a, y0b);
-      unpack2(frx, fxa, fxb);
-      unpack2(fry, fya, fyb);
+      unpack2(fla, x0a, y0a);
+      unpack2(flb, x0b, y0b);
+      unpack2(fra, fxa, fya);
+      unpack2(frb, fxb, fyb);
       // texels: w (x0, y0), z (x0+1, y0), x (x0, y0+1), y (x0+1, y0+1)
       const float4 ga = tex2Dgather<float4>(V.tex, x0a, y0a, 0);
       const float4 gb = tex2Dgather<float4>(V.tex, x0b, y0b, 0);
