@@ -128,7 +128,7 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
   const float zmin = pz - (float)kWinR * (fabsf(H6) + fabsf(H7));
   if (!(zmin > 0.f)) return kWorst;
   const float px = fmaf(H0, x, fmaf(H1, y, H2)), py = fmaf(H3, x, fmaf(H4, y, H5));
-  const float iz = 1.f / pz;
+  const float iz = rcp_approx(pz);
   const float cx = px * iz, cy = py * iz;
   if (!(cx >= 1.f && cx <= V.xmax && cy >= 1.f && cy <= V.ymax)) return kWorst;
   *evaluated += 1;
