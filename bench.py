@@ -52,20 +52,23 @@ FLOP_PER_PAIR_SETUP = 80
 FLOP_PER_PAIR = SAMPLES_PER_PAIR * FLOP_PER_SAMPLE + FLOP_PER_PAIR_SETUP
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum per phase launch from an ncu
-# capture, keyed by the hash of the kernel sources it was taken on (null
-# whenever the kernels changed since).
+# capture, keyed by the hash of the phase kernel's sources it was taken on
+# (null whenever they changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "4134fb56ec3fbbfd": 373866240.0 + 1420866000.0,   # profiles/phase_kernel_large.md
+    "61b8839d90488090": 271122432.0 + 240772864.0,   # profiles/phase_kernel_large.md
 }
 
 
+PHASE_KERNEL_SOURCES = ("amh_device.cuh", "amh_kernels.cu", "amh_kernels.h", "amh_update.cuh")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources the phase kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(REPO, "paper_1805_07920_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in PHASE_KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -283,6 +286,14 @@ def run_ours(args):
                 "flop_per_launch": flop_per_launch, "pairs_per_launch": pairs_phase / (2 * ITERS),
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                               f"(max SM clock)", "kernel_hash": khash}
+    # the second ceiling: one 2x2 texture gather per window sample, against the
+    # gather rate of this GPU measured in this run by a gather-only loop
+    gpeak = amh.gather_peak()
+    samples_per_s = pairs_phase / (2 * ITERS) * SAMPLES_PER_PAIR / (phase_ms * 1e-3)
+    roofline["fetch"] = {"bound": "texture gather", "achieved": round(samples_per_s / 1e12, 4),
+                         "peak": round(gpeak / 1e12, 4), "unit": "T samples/s",
+                         "frac": round(samples_per_s / gpeak, 4),
+                         "peak_basis": "amh_gather_peak: gather-only loop over update-like windows, measured live"}
 
     # end to end through the C-ABI with host buffers
     e2e = None

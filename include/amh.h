@@ -318,6 +318,14 @@ AMH_API void amh_net_destroy(amh_net* net);
 AMH_API int amh_read_maps_noalloc(amh_ctx* ctx, float* depth, float* normal3,
                                   int64_t first_pixel, int64_t n_pixels);
 
+/* The texture-gather ceiling of the current GPU, measured (this project's
+ * measurement utility, not part of the method): a loop of nothing but 2x2
+ * gathers of a uint8 texture laid out like the update's windows, 16 warps per
+ * SM; *samples_per_s receives gathers per second (one gather serves one
+ * window sample of Eq. (8)).  Synchronises the device; allocates and frees
+ * its own buffers. */
+AMH_API int amh_gather_peak(double* samples_per_s);
+
 /* Reference size, number of sources, current t. */
 AMH_API int amh_get_info(const amh_ctx* ctx, int32_t* width, int32_t* height,
                          int32_t* n_src, int32_t* t);

@@ -31,7 +31,7 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
            "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
            "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
-           "amh_net_last_error", "amh_net_destroy"]
+           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak"]
 
 
 class AmhError(RuntimeError):
@@ -93,6 +93,17 @@ def lib():
         L.amh_destroy.restype = None
         _LIB = L
     return _LIB
+
+
+def gather_peak() -> float:
+    """Measured texture-gather rate of the GPU (gathers per second)."""
+    L = lib()
+    L.amh_gather_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double()
+    rc = L.amh_gather_peak(ctypes.byref(v))
+    if rc != AMH_OK:
+        raise AmhError(rc, "gather peak measurement failed")
+    return v.value
 
 
 def default_params(**kw) -> Params:
