@@ -147,15 +147,39 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
+def assign_reference(sc, rank: int):
+    """The work of rank r: view (ref + r) mod n of the same scene as the
+    reference, its sources the other views by camera distance along the arc
+    (rank 0 keeps the scene's own reference and sources)."""
+    from paper_1805_07920_gb300 import synth
+    if not rank:
+        return sc
+    n = len(sc.cams)
+    ref = (sc.ref + rank) % n
+    src = sorted([v for v in range(n) if v != ref], key=lambda v: (abs(v - ref), v))[:len(sc.src)]
+    return synth.Scene(sc.name, sc.seed, sc.cams, sc.images, ref, src, sc.depth_min, sc.depth_max, {}, {})
+
+
 def rank_scene(rank: int):
     from paper_1805_07920_gb300 import synth
-    sc = synth.make_scene(SCENE)
-    if rank:
-        n = len(sc.cams)
-        ref = (sc.ref + rank) % n
-        src = sorted([v for v in range(n) if v != ref], key=lambda v: (abs(v - ref), v))
-        sc = synth.Scene(sc.name, sc.seed, sc.cams, sc.images, ref, src, sc.depth_min, sc.depth_max, {}, {})
-    return sc
+    return assign_reference(synth.make_scene(SCENE), rank)
+
+
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The slowest rank's time (the whole job's time); ms itself without a
+    process group."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(pixels: int, iters: int, steps: int, world: int, ms: float) -> float:
+    """Mpixel-iterations/s of the whole job: every rank updates `pixels`
+    pixels `iters` times per step."""
+    return pixels * iters * steps * world / (ms / 1e3) / 1e6
 
 
 def cpu_oracle_rate(sc, seconds: float, crop=(320, 212)):
@@ -266,12 +290,10 @@ def run_ours(args):
     clocks = clock.stop()
     ms = ev0.elapsed_time(ev1)
     phase_ms = float(np.mean([a.elapsed_time(b) for a, b in ph]))
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = W * H * ITERS * args.steps * world / (ms / 1e3) / 1e6
+    value = job_rate(W * H, ITERS, args.steps, world, ms)
 
     # roofline of the dominant kernel (the colour-phase kernel)
     props = torch.cuda.get_device_properties(local)
@@ -324,11 +346,8 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1e3
-        if dist:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": round(W * H * ITERS * args.e2e_steps * world / (e_ms / 1e3) / 1e6, 3), "unit": UNIT,
+        e_ms = max_over_ranks(e_ms, dist, "cuda")
+        e2e = {"value": round(job_rate(W * H, ITERS, args.e2e_steps, world, e_ms), 3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "amh_create from pinned host images + init + 6 iterations + amh_read_maps to pinned "
                        "host + amh_destroy"}
