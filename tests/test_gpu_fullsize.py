@@ -3,7 +3,10 @@ the launch configuration bench.py times: the GPU runs a whole colour phase;
 the FP64 oracle recomputes a sample of the updated pixels one by one from the
 same pre-phase state, and the two must keep the same plane with
 |dcost| <= 1e-4 on >= 99.9 % of the sampled pixels that are not near-ties.
+The same at full size with the images stored as FP16 (the precision form).
 The error statistics are printed (run with -s to see them)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -39,9 +42,11 @@ def _sample_pixels(W, H, color, n, rng):
     return np.concatenate([xs, bx[keep]]), np.concatenate([ys, by[keep]])
 
 
-@pytest.mark.parametrize("t,color", [(1, 0), (4, 1)])
-def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color):
+@pytest.mark.parametrize("t,color,f16", [(1, 0, False), (4, 1, False), (2, 0, True)])
+def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color, f16):
     sc = large_scene
+    if f16:
+        sc = dataclasses.replace(sc, images=[im.astype(np.float16) for im in sc.images])
     W, H = sc.width, sc.height
     g = amh.Context.from_scene(sc, seed=23)
     g.init_random()
@@ -74,7 +79,7 @@ def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color):
     n = len(xs)
     frac = n_ok / max(1, n - n_tie)
     dc = np.array(dc)
-    print(f"\nfull size t={t} colour={color}: {n} pixels, same plane and |dcost|<=1e-4 on {n_ok}, "
+    print(f"\nfull size t={t} colour={color} {'FP16' if f16 else 'uint8'} images: {n} pixels, same plane and |dcost|<=1e-4 on {n_ok}, "
           f"near-ties {n_tie}; |dcost| on same plane: median {np.median(dc):.2e}, "
           f"99.9% {np.quantile(dc, 0.999):.2e}, max {dc.max():.2e}")
     assert frac >= FRACTION, (n_ok, n_tie, n)
