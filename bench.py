@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched-form and learned-proposal measurements")
+                    help="skip the batched-form and learned-proposal measurements (run only at N = 1)")
     return ap.parse_args()
 
 
@@ -353,10 +353,9 @@ def run_ours(args):
                        "host + amh_destroy"}
 
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and world == 1:     # one-GPU measurements of the other forms
         extras["batched_ring20"] = bench_batch(args, dist)
-        if rank == 0:
-            extras["learned_proposal_1600x1056"] = bench_learned()
+        extras["learned_proposal_1600x1056"] = bench_learned()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

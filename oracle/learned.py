@@ -7,9 +7,10 @@ matching cost of Eq. (8) then judges as one more candidate.  This module
 writes its forward pass, loss and backward pass out plainly (3x3
 convolutions as sums over the nine taps, 2x2 average pooling, nearest
 upsampling, ReLU, additive skips, an L1 loss) so the CUDA kernels' outputs
-and gradients can be checked.  Where the kernels store BF16 (weights and
-stored activations) the oracle can round the same values to BF16
-(``bf16=True``) so the comparison isolates the arithmetic.
+and gradients can be checked.  Where the kernels store BF16 (weights, stored
+activations, the output gradients the weight and data gradients read) the
+oracle can round the same values to BF16 (``bf16=True``) so the comparison
+isolates the arithmetic.
 
 Layout: activations (H, W, C); conv weights (9, Cout, Cin) with tap
 t = 3 * (dy + 1) + (dx + 1); bias (Cout,).
@@ -133,7 +134,9 @@ def backward(cache, dout, bf16=False):
     g = {}
 
     def conv_bwd(name, x_in, dy, need_dx=True):
-        g[name] = conv3x3_wgrad(x_in, dy)
+        # weight and data gradients take dy as stored for the tensor cores
+        # (BF16 when bf16), the bias gradient the unrounded dy
+        g[name] = (conv3x3_wgrad(x_in, rnd(dy))[0], conv3x3_wgrad(x_in, dy)[1])
         return conv3x3_dgrad(rnd(dy), P[name][0]) if need_dx else None
 
     dd1 = conv_bwd("out", cache["in_out"], dout)

@@ -8,7 +8,8 @@
 // Kernels: 3x3 convolution forward on tensor cores (mma.sync m16n8k16, BF16
 // operands, FP32 accumulation, fused bias / ReLU / skip add), the data
 // gradient as the same convolution with flipped, transposed weights, the
-// weight gradient in FP32, 2x2 average pooling, nearest upsampling, the L1
+// weight gradient on tensor cores as well (BF16 operands, FP32 accumulation;
+// bias gradients in FP32), 2x2 average pooling, nearest upsampling, the L1
 // loss, Adam, and the feature / head / proposal conversions.
 //
 // Layout: activations (H, W, C) with C a multiple of 16, BF16 between
@@ -22,6 +23,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -126,56 +128,89 @@ __global__ void __launch_bounds__(128) conv3x3_fwd_kernel(const ConvArgs a) {
   }
 }
 
-// weight gradient in FP32: a block owns one tap and a 32 x 32 (co, ci) tile
-// and sums the chunks of kWgChunk pixels chunk0, chunk0 + stride, ...; warp
-// w takes co 4w .. 4w + 3, lane = ci.  The partial sums meet in dw / db by
-// atomics (one per block and output).
-constexpr int kWgChunk = 128;
-__global__ void __launch_bounds__(256) conv3x3_wgrad_kernel(const __nv_bfloat16* __restrict__ x,
-                                                           const float* __restrict__ dy, float* dw, float* db,
+// Weight gradient on tensor cores: dW[t] (Cout x Cin) = sum over pixels p of
+// dy(p)^T x(p + off(t)), BF16 operands (the BF16 copy of dy the data gradient
+// uses too), FP32 accumulation.  A block owns one tap and a 32 x 32 (co, ci)
+// tile and sums the chunks of kWgChunk pixels chunk0, chunk0 + stride, ...:
+// each chunk is staged transposed in shared memory (channel rows, pixel
+// columns, rows padded by 8 BF16 so the fragment loads are conflict-free);
+// warp w computes co (w / 2) * 16 .. + 15 x ci (w % 2) * 16 .. + 15 as one m16
+// tile and two n8 tiles.  The partial tiles meet in dw by atomics.
+constexpr int kWgChunk = 64;
+constexpr int kWgLd = kWgChunk + 8;
+__global__ void __launch_bounds__(128) conv3x3_wgrad_kernel(const __nv_bfloat16* __restrict__ x,
+                                                           const __nv_bfloat16* __restrict__ dy, float* dw,
                                                            int H, int W, int Cin, int Cout) {
-  __shared__ float sdy[kWgChunk][33];
-  __shared__ float sx[kWgChunk][33];
+  __shared__ __align__(16) __nv_bfloat16 sdy[32 * kWgLd];   // [co][px]
+  __shared__ __align__(16) __nv_bfloat16 sx[32 * kWgLd];    // [ci][px]
   const int t = blockIdx.z % 9, stride = gridDim.z / 9;
   const int co0 = blockIdx.y * 32, ci0 = blockIdx.x * 32;
   const int oy = t / 3 - 1, ox = t % 3 - 1;
   const int np = H * W, nchunks = (np + kWgChunk - 1) / kWgChunk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  float bsum = 0.f;
+  const int g = lane >> 2, tq = lane & 3;
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
+  float acc[2][4];
+#pragma unroll
+  for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+    for (int e = 0; e < 4; e++) acc[nt][e] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
   for (int chunk = blockIdx.z / 9; chunk < nchunks; chunk += stride) {
     const int p0 = chunk * kWgChunk;
     __syncthreads();
     for (int i = threadIdx.x; i < kWgChunk * 32; i += blockDim.x) {
-      const int pp = i / 32, c = i % 32;
-      const int p = p0 + pp;
-      float vdy = 0.f, vx = 0.f;
+      const int px = i / 32, c = i % 32;
+      const int p = p0 + px;
+      __nv_bfloat16 vdy = zero, vx = zero;
       if (p < np) {
-        const int py = p / W, pxx = p % W;
         if (co0 + c < Cout) vdy = dy[(size_t)p * Cout + co0 + c];
-        const int qy = py + oy, qx = pxx + ox;
-        if (ci0 + c < Cin && qy >= 0 && qy < H && qx >= 0 && qx < W)
-          vx = __bfloat162float(x[((size_t)qy * W + qx) * Cin + ci0 + c]);
+        const int qy = p / W + oy, qx = p % W + ox;
+        if (ci0 + c < Cin && qy >= 0 && qy < H && qx >= 0 && qx < W) vx = x[((size_t)qy * W + qx) * Cin + ci0 + c];
       }
-      sdy[pp][c] = vdy;
-      sx[pp][c] = vx;
+      sdy[c * kWgLd + px] = vdy;
+      sx[c * kWgLd + px] = vx;
     }
     __syncthreads();
-    for (int pp = 0; pp < kWgChunk; pp++) {
-      const float xv = sx[pp][lane];
 #pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fmaf(sdy[pp][warp * 4 + q], xv, acc[q]);
+    for (int k0 = 0; k0 < kWgChunk; k0 += 16) {
+      uint32_t af[4];
+      af[0] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g) * kWgLd + k0 + 2 * tq]);
+      af[1] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g + 8) * kWgLd + k0 + 2 * tq]);
+      af[2] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g) * kWgLd + k0 + 2 * tq + 8]);
+      af[3] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g + 8) * kWgLd + k0 + 2 * tq + 8]);
+#pragma unroll
+      for (int nt = 0; nt < 2; nt++) {
+        const __nv_bfloat16* br = &sx[(n0 + nt * 8 + g) * kWgLd + k0 + 2 * tq];
+        mma_bf16(acc[nt], af, *reinterpret_cast<const uint32_t*>(br), *reinterpret_cast<const uint32_t*>(br + 8));
+      }
     }
-    if (warp == 0)
-      for (int pp = 0; pp < kWgChunk; pp++) bsum += sdy[pp][lane];
   }
-  const int ci = ci0 + lane;
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int co = co0 + warp * 4 + q;
-    if (co < Cout && ci < Cin) atomicAdd(&dw[((size_t)t * Cout + co) * Cin + ci], acc[q]);
+  for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int co = co0 + m0 + g + (e >= 2 ? 8 : 0), ci = ci0 + n0 + nt * 8 + 2 * tq + (e & 1);
+      if (co < Cout && ci < Cin) atomicAdd(&dw[((size_t)t * Cout + co) * Cin + ci], acc[nt][e]);
+    }
+}
+
+// bias gradient in FP32: db[c] = sum over pixels of dy(p, c)
+__global__ void __launch_bounds__(256) bias_grad_kernel(const float* __restrict__ dy, int np, int C,
+                                                        int per_block, float* db) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31), r = threadIdx.x >> 5;
+  const int p0 = blockIdx.y * per_block, p1 = min(np, p0 + per_block);
+  float s = 0.f;
+  if (c < C)
+    for (int p = p0 + r; p < p1; p += 8) s += dy[(size_t)p * C + c];
+  red[r][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (r == 0) {
+    float tot = 0.f;
+    for (int q = 0; q < 8; q++) tot += red[q][threadIdx.x & 31];
+    if (c < C) atomicAdd(&db[c], tot);
   }
-  if (t == 4 && blockIdx.x == 0 && warp == 0 && co0 + lane < Cout) atomicAdd(&db[co0 + lane], bsum);
 }
 
 // weights (9, Cout, Cin) -> data-gradient weights (9, Cin, Cout), taps flipped
@@ -405,24 +440,31 @@ int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float
          __nv_bfloat16* y16, __nv_bfloat16* r16, float* y32, int H, int W, int Cin, int Cout, int relu) {
   ConvArgs a{x, w, bias, skip, y16, r16, y32, H, W, Cin, Cout, relu};
   const size_t smem = (size_t)9 * 32 * (Cin + 8) * sizeof(__nv_bfloat16);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the largest weight tile (Cin = 128) needs more than the default 48 KB;
+  // the attribute is per device, so set it for each device a network uses
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(once[dev & 63], [] {
     cudaFuncSetAttribute(conv3x3_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 32 * (128 + 8) * 2);
-    attr_set = true;
-  }
+  });
   dim3 grid((W + 63) / 64, H, (Cout + 31) / 32);
   conv3x3_fwd_kernel<<<grid, 128, smem, n->stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
   return AMH_OK;
 }
-void wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, int H, int W) {
-  const int Cin = kNet[L].cin, Cout = kNet[L].cout;
+// weight gradient of layer L from its input x and its output gradient (FP32
+// dy for the bias, its BF16 copy dy16 for the weights)
+void wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, const __nv_bfloat16* dy16, int H, int W) {
+  const int Cin = kNet[L].cin, Cout = kNet[L].cout, np = H * W;
   // enough blocks to fill the GPU a few times over; each strides over chunks
-  const int tiles = ((Cin + 31) / 32) * ((Cout + 31) / 32), nchunks = (H * W + kWgChunk - 1) / kWgChunk;
-  const int groups = std::max(1, std::min(nchunks, 4096 / (9 * tiles)));
+  const int tiles = ((Cin + 31) / 32) * ((Cout + 31) / 32), nchunks = (np + kWgChunk - 1) / kWgChunk;
+  const int groups = std::max(1, std::min(nchunks, 2048 / (9 * tiles)));
   dim3 grid((Cin + 31) / 32, (Cout + 31) / 32, 9 * groups);
-  conv3x3_wgrad_kernel<<<grid, 256, 0, n->stream>>>(x, dy, n->gw[L], n->gb[L], H, W, Cin, Cout);
+  conv3x3_wgrad_kernel<<<grid, 128, 0, n->stream>>>(x, dy16, n->gw[L], H, W, Cin, Cout);
+  const int per_block = 2048, nb = (np + per_block - 1) / per_block;
+  bias_grad_kernel<<<dim3((Cout + 31) / 32, nb), 256, 0, n->stream>>>(dy, np, Cout, per_block, n->gb[L]);
 }
 // data gradient of layer L: dx (FP32, H x W x Cin) from dy (BF16 copy in g16)
 int dgrad(amh_net* n, int L, const __nv_bfloat16* dy16, float* dx, int H, int W) {
@@ -617,39 +659,39 @@ AMH_API int amh_net_backward(amh_net* n, float* loss_out) {
   float* const* dy = n->dy;
   l1_loss_kernel<<<blocks_for(P0), 256, 0, s>>>(n->out, n->target, n->mask, dy[7], n->loss, (int)P0, inv_n);
   // out = conv(d1)
-  wgrad(n, 7, n->d1, dy[7], H0, W0);
   to_bf16_kernel<<<blocks_for(P0 * 16), 256, 0, s>>>(dy[7], n->g16, P0 * 16);
+  wgrad(n, 7, n->d1, dy[7], n->g16, H0, W0);
   int rc = dgrad(n, 7, n->g16, n->gA, H0, W0);                       // gA = d d1 (P0 x 32)
   // d1 = relu(conv(in_d1)) + e1
   NTRY(n, cudaMemcpyAsync(n->gE1, n->gA, P0 * 32 * 4, cudaMemcpyDeviceToDevice, s));
   relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gA, n->r1, dy[6], n->g16, P0 * 32);
-  wgrad(n, 6, n->in_d1, dy[6], H0, W0);
+  wgrad(n, 6, n->in_d1, dy[6], n->g16, H0, W0);
   if (!rc) rc = dgrad(n, 6, n->g16, n->gA, H0, W0);                  // d in_d1 (P0 x 64)
   up2_bwd_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gA, n->gE2, H1, W1, 64);  // d d2 (P1 x 64)
   relu_mask_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gE2, n->r2, dy[5], n->g16, P1 * 64);
-  wgrad(n, 5, n->in_d2, dy[5], H1, W1);
+  wgrad(n, 5, n->in_d2, dy[5], n->g16, H1, W1);
   if (!rc) rc = dgrad(n, 5, n->g16, n->gA, H1, W1);                  // d in_d2 (P1 x 96)
   up2_bwd_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gA, n->gE3, H2, W2, 96);  // d d3 (P2 x 96)
   relu_mask_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gE3, n->r3, dy[4], n->g16, P2 * 96);
-  wgrad(n, 4, n->in_d3, dy[4], H2, W2);
+  wgrad(n, 4, n->in_d3, dy[4], n->g16, H2, W2);
   if (!rc) rc = dgrad(n, 4, n->g16, n->gA, H2, W2);                  // d in_d3 (P2 x 128)
   up2_bwd_kernel<<<blocks_for(P3 * 128), 256, 0, s>>>(n->gA, n->gB, H3, W3, 128); // d e4 (P3 x 128)
   // e4 = relu(conv(in_e4))
   relu_mask_kernel<<<blocks_for(P3 * 128), 256, 0, s>>>(n->gB, n->e4, dy[3], n->g16, P3 * 128);
-  wgrad(n, 3, n->in_e4, dy[3], H3, W3);
+  wgrad(n, 3, n->in_e4, dy[3], n->g16, H3, W3);
   if (!rc) rc = dgrad(n, 3, n->g16, n->gA, H3, W3);                  // d in_e4 (P3 x 96)
   pool2_bwd_add_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gA, n->gE3, H2, W2, 96);
   // e3 = relu(conv(in_e3)), read by d3 (skip) and by the pooling
   relu_mask_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gE3, n->e3, dy[2], n->g16, P2 * 96);
-  wgrad(n, 2, n->in_e3, dy[2], H2, W2);
+  wgrad(n, 2, n->in_e3, dy[2], n->g16, H2, W2);
   if (!rc) rc = dgrad(n, 2, n->g16, n->gA, H2, W2);                  // d in_e3 (P2 x 64)
   pool2_bwd_add_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gA, n->gE2, H1, W1, 64);
   relu_mask_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gE2, n->e2, dy[1], n->g16, P1 * 64);
-  wgrad(n, 1, n->in_e2, dy[1], H1, W1);
+  wgrad(n, 1, n->in_e2, dy[1], n->g16, H1, W1);
   if (!rc) rc = dgrad(n, 1, n->g16, n->gA, H1, W1);                  // d in_e2 (P1 x 32)
   pool2_bwd_add_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gA, n->gE1, H0, W0, 32);
-  relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gE1, n->e1, dy[0], nullptr, P0 * 32);
-  wgrad(n, 0, n->x0, dy[0], H0, W0);
+  relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gE1, n->e1, dy[0], n->g16, P0 * 32);
+  wgrad(n, 0, n->x0, dy[0], n->g16, H0, W0);
   if (rc) return rc;
   NTRY(n, cudaGetLastError());
   if (loss_out) {

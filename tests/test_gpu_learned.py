@@ -162,13 +162,15 @@ def test_every_operation_elementwise(amh):
     g = net.get_grads()
     inputs = {"e1": "x0", "e2": "in_e2", "e3": "in_e3", "e4": "in_e4", "d3": "in_d3", "d2": "in_d2",
               "d1": "in_d1", "out": "d1"}
+    b16 = OL.bf16_round
     for L, xin in inputs.items():
-        dw, db = OL.conv3x3_wgrad(G[xin], D[L])
-        sw, sb = OL.conv3x3_wgrad(np.abs(G[xin]), np.abs(D[L]))
+        dw = OL.conv3x3_wgrad(G[xin], b16(D[L]))[0]          # tensor cores: BF16 dy
+        db = OL.conv3x3_wgrad(G[xin], D[L])[1]               # FP32 bias sums
+        sw = OL.conv3x3_wgrad(np.abs(G[xin]), np.abs(b16(D[L])))[0]
+        sb = OL.conv3x3_wgrad(np.abs(G[xin]), np.abs(D[L]))[1]
         _check_acc(g[L][0], dw, sw, f"dW {L}", k=1e-4)
         _check_acc(g[L][1], db, sb, f"db {L}", k=1e-4)
     # data gradients: each layer's masked output gradient from the next one's
-    b16 = OL.bf16_round
 
     def dg(L):   # d (input of L) from L's stored output gradient, and its term-sum scale
         return OL.conv3x3_dgrad(b16(D[L]), Pw[L]), OL.conv3x3_dgrad(np.abs(b16(D[L])), absw[L])
