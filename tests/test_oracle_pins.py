@@ -546,3 +546,34 @@ def test_own_plane_wins_exact_ties(oracle_mod, tiny_scene):
     for (x, y) in [(20, 20), (50, 60), (101, 33), (140, 100)]:
         u = o.update_pixel(x, y)
         assert u["choice"] >= 8
+
+
+def test_score_plane_is_eq7_from_pinned_parts(oracle_mod, tiny_scene):
+    """score_plane (the oracle's judge of near-ties) is Eq. (7) for one plane:
+    rebuilt here from the separately pinned parts -- the 8 ACP rows, the cost
+    of Eq. (8) per view, the view weights of Eqs. (2)-(6) -- as
+    sum_j w_j m(plane, j) / sum_j w_j; invalid rows count as cost 2 and stay
+    out of the view selection."""
+    sc = tiny_scene
+    o = oracle_mod.Oracle.from_scene(sc, seed=15)
+    o.init_random()
+    o.iterate(1)
+    st = o.get_state()
+    N = len(sc.src)
+    rng = np.random.default_rng(15)
+    for _ in range(12):
+        x, y = int(rng.integers(0, sc.width)), int(rng.integers(0, sc.height))
+        M = np.full((8, N), 2.0)
+        valid = np.zeros(8, np.int32)
+        for g in range(8):
+            row = o.acp_row(x, y, g)
+            if row is None:
+                continue
+            valid[g] = 1
+            M[g] = [o.cost(x, y, row, j) for j in range(N)]
+        w, _, _ = oracle_mod.mhj(M, row_valid=valid, t=st["t"], S_prev=int(st["sel"][y, x]),
+                                 v_prev=int(st["vprev"][y, x]), params=o.params)
+        assert w.sum() > 0
+        for plane in (st["plane"][y, x], o.random_plane(x, y)):
+            expect = sum(w[j] * o.cost(x, y, plane, j) for j in range(N) if w[j] > 0) / w.sum()
+            assert o.score_plane(x, y, plane) == pytest.approx(expect, rel=1e-12, abs=1e-15)
