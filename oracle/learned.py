@@ -3,7 +3,7 @@
 The network is this project's extension, not the paper's: a 4-level
 convolutional encoder-decoder that reads the half-resolution state of the
 checkerboard update and proposes one plane per pixel, which the unchanged
-matching cost of Eq. (8) then judges as one more candidate.  This module
+matching cost of Eq. (8) then scores as one more candidate.  This module
 writes its forward pass, loss and backward pass out plainly (3x3
 convolutions as sums over the nine taps, 2x2 average pooling, nearest
 upsampling, ReLU, additive skips, an L1 loss) so the CUDA kernels' outputs

@@ -437,7 +437,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 
   // --- Sec. 3.3: refinement with the same weights -------------------------------------
   // A learned proposal (n, d) of this pixel's 2 x 2 block, when present, is one
-  // more candidate after the refinement ones, judged by the same weights.
+  // more candidate after the refinement ones, scored with the same weights.
   const int nc = a.t < 3 ? 1 : kMaxRefine;
   float4 prop = make_float4(0.f, 0.f, 0.f, 0.f);
   bool has_prop = false;

@@ -5,7 +5,7 @@ checkerboard update has reached after ``T_IN`` iterations (on the
 half-resolution grid) and predicts the residuals towards the state the plain
 method reaches after its full ``T_FINAL`` iterations (Sec. 4 runs 6).  Its
 proposal joins one following iteration as an extra candidate that the
-unchanged matching cost judges, so the plain method stays the arbiter.
+unchanged matching cost scores, so the plain method stays the arbiter.
 
 Training data is the plain method's own output on seeded synthetic scenes (no
 ground truth is used for training); the forward pass, every gradient and the

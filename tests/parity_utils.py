@@ -76,7 +76,7 @@ def valid_pixels(scene, margin=5):
 
 def phase_check(orc, ctx, st, color):
     """Identical state into both, one phase on each, per-pixel comparison with
-    near-ties judged by the oracle.  Returns the report of compare_phase plus
+    near-ties decided by the oracle.  Returns the report of compare_phase plus
     'ties' and 'frac_ok_nontie'."""
     load_identical(orc, ctx, st)
     orc.step_phase(color)
@@ -85,7 +85,7 @@ def phase_check(orc, ctx, st, color):
     o_st, g_st = orc.get_state(), ctx.get_state()
     mask = color_mask(ctx.H, ctx.W, color)
     r = compare_phase(o_st, g_st, mask)
-    # judge the disagreements against the pre-phase state
+    # classify the disagreements against the pre-phase state
     s = fp32_state(st)
     orc.set_state(plane=s["plane"], cost=s["cost"], sel=s["sel"], vprev=s["vprev"], t=s["t"])
     dcost = np.abs(o_st["cost"] - g_st["cost"].astype(np.float64))

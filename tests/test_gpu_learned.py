@@ -2,7 +2,7 @@
 every weight / bias gradient of the BF16 tensor-core kernels against the FP64
 oracle (oracle/learned.py, BF16 rounding emulated at the same points), Adam
 against PyTorch's CPU Adam, the feature / target / head conversions, and the
-injection of the proposal into the checkerboard update (a candidate judged by
+injection of the proposal into the checkerboard update (a candidate scored by
 the unchanged cost, leaving every other pixel as the plain method has it).
 
 Tolerances: the kernels accumulate in FP32 where the oracle uses FP64, so a

@@ -549,7 +549,7 @@ def test_own_plane_wins_exact_ties(oracle_mod, tiny_scene):
 
 
 def test_score_plane_is_eq7_from_pinned_parts(oracle_mod, tiny_scene):
-    """score_plane (the oracle's judge of near-ties) is Eq. (7) for one plane:
+    """score_plane (what classifies near-ties in the parity tests) is Eq. (7) for one plane:
     rebuilt here from the separately pinned parts -- the 8 ACP rows, the cost
     of Eq. (8) per view, the view weights of Eqs. (2)-(6) -- as
     sum_j w_j m(plane, j) / sum_j w_j; invalid rows count as cost 2 and stay
