@@ -16,6 +16,9 @@ ORACLE_DIR = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(ORACLE_DIR, "_lib", "liborc.so")
 ORC_MAX_SRC = 32
 NREGION = 8
+ORC_FLAG_SQUARED = 1        # squared differences in the bilateral weight
+ORC_FLAG_SYMMETRIC = 4      # ablation: symmetric checkerboard propagation
+ORC_FLAG_HEURISTIC = 8      # ablation: heuristic (per-hypothesis k-best) view selection
 
 
 def build_command() -> list[str]:
@@ -88,6 +91,8 @@ def lib():
                               ctypes.c_uint32, ctypes.c_int, _vp, _vp, _vp]
         L.orc_acp_offsets.restype = ctypes.c_int
         L.orc_acp_offsets.argtypes = [ctypes.c_int, _vp, _vp]
+        L.orc_scp_offsets.restype = ctypes.c_int
+        L.orc_scp_offsets.argtypes = [ctypes.c_int, _vp, _vp]
         L.orc_acp_pick.restype = ctypes.c_int
         L.orc_acp_pick.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.orc_acp_row.restype = ctypes.c_int
@@ -145,6 +150,14 @@ def acp_offsets(g: int):
     dy = np.zeros(16, np.int32)
     n = lib().orc_acp_offsets(g, _ptr(dx), _ptr(dy))
     return list(zip(dx[:n].tolist(), dy[:n].tolist()))
+
+
+def scp_offsets(g: int):
+    """The fixed candidate of region g under symmetric propagation."""
+    dx = np.zeros(1, np.int32)
+    dy = np.zeros(1, np.int32)
+    lib().orc_scp_offsets(g, _ptr(dx), _ptr(dy))
+    return [(int(dx[0]), int(dy[0]))]
 
 
 def mhj(M, row_valid=None, t=0, S_prev=0, v_prev=-1, params: OrcParams | None = None):

@@ -339,11 +339,24 @@ int orc_acp_offsets(int g, int* dx, int* dy) {
   return n;
 }
 
+/* Symmetric checkerboard propagation, the ablation "\\ACP" of Sec. 4 (the
+ * paper names Gipuma's diffusion-like scheme but draws it only in the
+ * missing Fig. 2(b, c)); reading: region g holds one fixed candidate, the
+ * axis neighbour at distance 1 (g = 0..3) or 5 (g = 4..7) in the direction
+ * up, down, left, right -- odd distances, so the opposite colour. */
+int orc_scp_offsets(int g, int* dx, int* dy) {
+  static const int ax[4] = {0, 0, -1, 1}, ay[4] = {-1, 1, 0, 0};
+  const int dist = g < 4 ? 1 : 5;
+  dx[0] = ax[g & 3] * dist;
+  dy[0] = ay[g & 3] * dist;
+  return 1;
+}
+
 /* the candidate of region g with the lowest current matching cost (Sec. 3.1:
  * the lower the cost, the more likely the hypothesis is true) */
 int orc_acp_pick(const orc_ctx* c, int x, int y, int g) {
   int dx[16], dy[16];
-  int n = orc_acp_offsets(g, dx, dy);
+  int n = (c->p.flags & ORC_FLAG_SYMMETRIC) ? orc_scp_offsets(g, dx, dy) : orc_acp_offsets(g, dx, dy);
   int best = -1;
   double bc = 0;
   for (int i = 0; i < n; i++) {
@@ -543,7 +556,10 @@ static void pixel_weights(const orc_ctx* c, int x, int y, double rows[][4], int*
 
 /* unified cost (Eq. 7) of an arbitrary plane at (x, y) under the weights this
  * pixel's update would use -- for judging near-ties in parity checks */
+static double kbest_cost(const orc_ctx* c, int x, int y, const double pl[4]);
+
 double orc_score_plane(const orc_ctx* c, int x, int y, const double plane[4]) {
+  if (c->p.flags & ORC_FLAG_HEURISTIC) return kbest_cost(c, x, y, plane);
   double rows[ORC_NREGION][4], M[ORC_NREGION * ORC_MAX_SRC], w[ORC_MAX_SRC], sw;
   int valid[ORC_NREGION];
   uint32_t S;
@@ -552,8 +568,70 @@ double orc_score_plane(const orc_ctx* c, int x, int y, const double plane[4]) {
   return weighted_cost(c, x, y, plane, w, sw);
 }
 
+/* mean of the k smallest per-view costs of a plane, summed in ascending order
+ * (ties: lower view) -- the heuristic view selection of Sec. 2 */
+static double kbest_mean(const orc_ctx* c, const double* m) {
+  const int N = c->n_src;
+  int k = c->p.k < N ? c->p.k : N;
+  int used[ORC_MAX_SRC] = {0};
+  double a = 0;
+  for (int r = 0; r < k; r++) {
+    int b = -1;
+    for (int j = 0; j < N; j++)
+      if (!used[j] && (b < 0 || m[j] < m[b])) b = j;
+    used[b] = 1;
+    a += m[b];
+  }
+  return a / k;
+}
+
+static double kbest_cost(const orc_ctx* c, int x, int y, const double pl[4]) {
+  double m[ORC_MAX_SRC];
+  for (int j = 0; j < c->n_src; j++) m[j] = orc_cost(c, x, y, pl, j);
+  return kbest_mean(c, m);
+}
+
+/* The ablation "\\MHJ" of Sec. 4, reading: every hypothesis -- the 8
+ * propagated rows, the pixel's own plane, the refinement candidates -- is
+ * scored by the mean of its own k smallest per-view costs (no joint view
+ * selection, no S_t or v_t); the rest of the update is unchanged. */
+static void update_pixel_heuristic(const orc_ctx* c, int x, int y, double out[4], double* cost_out,
+                                   uint32_t* sel_out, int32_t* v_out, int32_t* choice_out) {
+  const int N = c->n_src;
+  size_t pi = (size_t)y * c->W + x;
+  double best[4];
+  memcpy(best, &c->plane[4 * pi], sizeof best);
+  double bm = kbest_cost(c, x, y, best);
+  int choice = 8;
+  for (int g = 0; g < ORC_NREGION; g++) {
+    double row[4], m[ORC_MAX_SRC];
+    if (!orc_acp_row(c, x, y, g, row)) continue;
+    for (int j = 0; j < N; j++) m[j] = orc_cost(c, x, y, row, j);
+    double a = kbest_mean(c, m);
+    if (a < bm) { bm = a; memcpy(best, row, sizeof best); choice = g; }
+  }
+  double cand[ORC_MAX_REFINE][4];
+  int nc = orc_refine_candidates(c, x, y, best, c->t, cand);
+  int bc = -1;
+  double bcm = 0;
+  for (int i = 0; i < nc; i++) {
+    double a = kbest_cost(c, x, y, cand[i]);
+    if (bc < 0 || a < bcm) { bc = i; bcm = a; }
+  }
+  if (bc >= 0 && bcm < bm) { bm = bcm; memcpy(best, cand[bc], sizeof best); choice = 9 + bc; }
+  memcpy(out, best, sizeof best);
+  *cost_out = bm;
+  *sel_out = 0;
+  *v_out = -1;
+  *choice_out = choice;
+}
+
 void orc_update_pixel(const orc_ctx* c, int x, int y, double out[4], double* cost_out,
                       uint32_t* sel_out, int32_t* v_out, int32_t* choice_out) {
+  if (c->p.flags & ORC_FLAG_HEURISTIC) {
+    update_pixel_heuristic(c, x, y, out, cost_out, sel_out, v_out, choice_out);
+    return;
+  }
   const int N = c->n_src;
   size_t pi = (size_t)y * c->W + x;
   /* Sec. 3.1: eight propagated hypotheses; Eqs. (1)-(6): view weights */

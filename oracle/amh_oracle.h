@@ -54,8 +54,14 @@ typedef struct {
   int win_radius, win_stride;/* 5, 2: 11x11 window, every other row/column    */
   double depth_min, depth_max;
   uint64_t seed;
-  int flags;                 /* bit 0: squared bilateral differences          */
+  int flags;                 /* bit 0: squared bilateral differences;
+                                bit 2: symmetric propagation (ablation
+                                "\\ACP" of Sec. 4); bit 3: heuristic view
+                                selection (ablation "\\MHJ" of Sec. 4)       */
 } orc_params;
+
+#define ORC_FLAG_SYMMETRIC 4
+#define ORC_FLAG_HEURISTIC 8
 
 typedef struct orc_ctx orc_ctx;
 
@@ -107,6 +113,7 @@ void   orc_mhj(const orc_params* p, int t, const double* M, const int* row_valid
                uint32_t* S_out, int32_t* v_out);
 /* candidate offsets of ACP region g (0..3 near up/down/left/right, 4..7 far) */
 int    orc_acp_offsets(int g, int* dx, int* dy);
+int    orc_scp_offsets(int g, int* dx, int* dy);
 /* index y*W+x of the picked candidate of region g, or -1 if none in image */
 int    orc_acp_pick(const orc_ctx* c, int x, int y, int g);
 /* propagated hypothesis of region g at pixel (x, y); 0 if the row is invalid */

@@ -577,3 +577,53 @@ def test_score_plane_is_eq7_from_pinned_parts(oracle_mod, tiny_scene):
         for plane in (st["plane"][y, x], o.random_plane(x, y)):
             expect = sum(w[j] * o.cost(x, y, plane, j) for j in range(N) if w[j] > 0) / w.sum()
             assert o.score_plane(x, y, plane) == pytest.approx(expect, rel=1e-12, abs=1e-15)
+
+
+def test_symmetric_propagation_geometry(oracle_mod, tiny_scene):
+    """The ablation without ACP: eight fixed candidates, the axis neighbours at
+    distances 1 and 5 -- symmetric, opposite colour, no choice by cost."""
+    offs = [oracle_mod.scp_offsets(g)[0] for g in range(8)]
+    assert set(offs) == {(0, -1), (0, 1), (-1, 0), (1, 0), (0, -5), (0, 5), (-5, 0), (5, 0)}
+    assert all((abs(dx) + abs(dy)) % 2 == 1 for dx, dy in offs)
+    assert all((-dx, -dy) in offs for dx, dy in offs)
+    sc = tiny_scene
+    p = oracle_mod.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=3,
+                                  flags=oracle_mod.ORC_FLAG_SYMMETRIC)
+    o = oracle_mod.Oracle.from_scene(sc, p)
+    H, W = sc.height, sc.width
+    o.set_state(plane=np.tile([0.0, 0.0, -1.0, 5.0], (H, W, 1)),
+                cost=np.random.default_rng(4).uniform(0, 2, (H, W)), t=0)
+    for (x, y) in [(10, 10), (2, 60), (157, 3), (80, 118)]:
+        for g, (dx, dy) in enumerate(offs):
+            qx, qy = x + dx, y + dy
+            expect = qy * W + qx if 0 <= qx < W and 0 <= qy < H else -1
+            assert o.acp_pick(x, y, g) == expect
+
+
+@pytest.mark.parametrize("flags", ["heuristic", "both"])
+def test_heuristic_view_selection(oracle_mod, tiny_scene, flags):
+    """The ablation without MHJ: every hypothesis scored by the mean of its own
+    k = 4 smallest per-view costs; the update keeps the smallest (own plane on
+    ties), refinement included, and records no view selection."""
+    sc = tiny_scene
+    f = oracle_mod.ORC_FLAG_HEURISTIC | (oracle_mod.ORC_FLAG_SYMMETRIC if flags == "both" else 0)
+    p = oracle_mod.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=5, flags=f)
+    o = oracle_mod.Oracle.from_scene(sc, p)
+    o.init_random()
+    o.iterate(1)
+    st = o.get_state()
+    N = len(sc.src)
+    kb = lambda pl: float(np.mean(np.sort([o.cost(x, y, pl, j) for j in range(N)])[:min(4, N)]))
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        x, y = int(rng.integers(0, sc.width)), int(rng.integers(0, sc.height))
+        u = o.update_pixel(x, y)
+        assert u["sel"] == 0 and u["v"] == -1
+        assert u["cost"] == pytest.approx(kb(u["plane"]), rel=1e-12, abs=1e-15)
+        own = kb(st["plane"][y, x])
+        assert u["cost"] <= own + 1e-15
+        for g in range(8):
+            row = o.acp_row(x, y, g)
+            if row is not None:
+                assert u["cost"] <= kb(row) + 1e-15
+        assert o.score_plane(x, y, u["plane"]) == pytest.approx(u["cost"], rel=1e-12, abs=1e-15)
