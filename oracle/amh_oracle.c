@@ -285,15 +285,21 @@ double orc_cost(const orc_ctx* c, int x, int y, const double plane[4], int j) {
       double r = c->img_ref[(size_t)yr * W + xr];
       double dI = fabs(r - Ic), dx = sqrt((double)(du * du + dv * dv));
       if (p->flags & 1) { dI = dI * dI; dx = dx * dx; }
-      double w = exp(-dI / (2.0 * p->sigma_I * p->sigma_I) - dx / (2.0 * p->sigma_x * p->sigma_x));
+      double e = dI / (2.0 * p->sigma_I * p->sigma_I) + dx / (2.0 * p->sigma_x * p->sigma_x);
       double u = x + du, v = y + dv;
       double z = H[6] * u + H[7] * v + H[8];
       double sx = (H[0] * u + H[1] * v + H[2]) / z, sy = (H[3] * u + H[4] * v + H[5]) / z;
       rr[nk] = r;
       ss[nk] = orc_bilinear(c->img_src[j], c->Ws[j], c->Hs[j], sx, sy);
-      ww[nk] = w;
+      ww[nk] = e;
       nk++;
     }
+  /* w = exp(-e), taken relative to the largest weight: every statistic of
+   * Eq. (8) is a ratio of weighted sums, so a common factor cancels, and no
+   * weight underflows (squared 8-bit differences reach e = 3600) */
+  double emin = ww[0];
+  for (int k = 1; k < nk; k++) emin = ww[k] < emin ? ww[k] : emin;
+  for (int k = 0; k < nk; k++) ww[k] = exp(-(ww[k] - emin));
   /* weighted averages E(x) = sum w x / sum w, then the weighted covariances */
   double sw = 0, er = 0, es = 0;
   for (int k = 0; k < nk; k++) { sw += ww[k]; er += ww[k] * rr[k]; es += ww[k] * ss[k]; }
