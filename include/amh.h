@@ -63,10 +63,20 @@ enum { AMH_MEM_HOST = 0, AMH_MEM_DEVICE = 1 };
 /* parameter flags */
 enum {
   AMH_FLAG_BILATERAL_SQUARED = 1, /* use dI^2 and dx^2 in the bilateral weight  */
-  AMH_FLAG_IMAGES_F16 = 2         /* images are IEEE binary16 (2 bytes/pixel,
+  AMH_FLAG_IMAGES_F16 = 2,        /* images are IEEE binary16 (2 bytes/pixel,
                                      intensities in any unit) instead of uint8;
                                      they are stored as FP16 textures, the
                                      interpolation and NCC moments stay FP32   */
+  /* The ablations of Sec. 4 (Table 2, columns "\ACP" and "\MHJ"); single
+   * contexts only (amh_batch_create rejects them). */
+  AMH_FLAG_SYMMETRIC_PROPAGATION = 4, /* instead of ACP (Sec. 3.1): region g
+                                     is one fixed candidate, the axis
+                                     neighbour at distance 1 (g = 0..3) or 5
+                                     (g = 4..7) up / down / left / right    */
+  AMH_FLAG_HEURISTIC_VIEWS = 8    /* instead of MHJ (Sec. 3.2): every
+                                     hypothesis is scored by the mean of its
+                                     own k smallest per-view costs; no S_t or
+                                     v_t is kept (sel 0, vbest 255)           */
 };
 
 typedef struct amh_ctx amh_ctx;

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 AMH_OK, AMH_EINVAL, AMH_ECUDA, AMH_ENOMEM, AMH_EDEVICE, AMH_ESTATE = 0, -1, -2, -3, -4, -5
 AMH_MEM_HOST, AMH_MEM_DEVICE = 0, 1
 AMH_FLAG_BILATERAL_SQUARED = 1
+AMH_FLAG_SYMMETRIC_PROPAGATION = 4   # ablation: symmetric checkerboard propagation
+AMH_FLAG_HEURISTIC_VIEWS = 8         # ablation: per-hypothesis k-best view selection
 AMH_FLAG_IMAGES_F16 = 2
 MAX_SRC = 32
 NOALLOC_MAX_PIXELS = 262144

@@ -220,6 +220,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   a.wX = (float)(1.0 / (2.0 * (double)p->sigma_x * p->sigma_x));
   a.squared = (p->flags & AMH_FLAG_BILATERAL_SQUARED) ? 1 : 0;
   a.img_half = half ? 1 : 0;
+  a.ablation = ((p->flags & AMH_FLAG_SYMMETRIC_PROPAGATION) ? 1 : 0) | ((p->flags & AMH_FLAG_HEURISTIC_VIEWS) ? 2 : 0);
   a.dmin = p->depth_min;
   a.dmax = p->depth_max;
   a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);

@@ -308,6 +308,8 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
   if (!(p->k >= 1) || p->n1 < 0 || p->n2 < 0 || !(p->beta > 0) || !(p->sigma_I > 0) || !(p->sigma_x > 0) ||
       !(p->alpha > 0) || !(p->depth_min > 0) || !(p->depth_max > p->depth_min))
     return bfail(nullptr, AMH_EINVAL, "invalid parameters");
+  if (p->flags & (AMH_FLAG_SYMMETRIC_PROPAGATION | AMH_FLAG_HEURISTIC_VIEWS))
+    return bfail(nullptr, AMH_EINVAL, "the ablation flags apply to single contexts only");
   if (src_offsets[0] != 0) return bfail(nullptr, AMH_EINVAL, "src_offsets[0] must be 0");
   for (int r = 0; r < n_refs; r++) {
     const int ref = refs[r];

@@ -45,6 +45,7 @@ struct PhaseArgs {
   float wI, wX;              // 1 / (2 sigma_I^2), 1 / (2 sigma_x^2), Eq. (8)
   int squared;               // bilateral weight on squared differences
   int img_half;              // images are FP16 (else uint8)
+  int ablation;              // bit 0: symmetric propagation, bit 1: heuristic views (Sec. 4)
   float dmin, dmax;
   uint32_t key0, key1;       // Philox key (seed)
   const void* ref;           // reference image, W x H (uint8 or FP16)

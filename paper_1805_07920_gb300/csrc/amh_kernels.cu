@@ -22,14 +22,14 @@ __device__ __forceinline__ void count_pairs(const PhaseArgs& a, int npairs) {
               (unsigned long long)tot);
 }
 
-template <bool kHalf>
+template <bool kHalf, int kMode>
 __global__ void __launch_bounds__(kThreads, kPhaseBlocksPerSM) phase_kernel(const __grid_constant__ PhaseArgs a) {
   PixelArrays sm;
   const int tid = threadIdx.x;
   const int y = blockIdx.y * kTile + (tid >> 3);
   const int x = blockIdx.x * kTile + 2 * (tid & 7) + ((y + a.color) & 1);
   int npairs = 0;
-  if (x < a.W && y < a.H) update_pixel<kHalf>(a, sm, x, y, &npairs);
+  if (x < a.W && y < a.H) update_pixel<kHalf, kMode>(a, sm, x, y, &npairs);
   count_pairs(a, npairs);
 }
 
@@ -64,16 +64,27 @@ int launch_init(const PhaseArgs& a, cudaStream_t s) {
   return a.img_half ? launch_init_t<true>(a, s) : launch_init_t<false>(a, s);
 }
 
-template <bool kHalf>
+template <bool kHalf, int kMode>
 int launch_phase_t(const PhaseArgs& a, cudaStream_t s) {
-  static bool once = (prefer_l1(phase_kernel<kHalf>), true);
+  static bool once = (prefer_l1(phase_kernel<kHalf, kMode>), true);
   (void)once;
   dim3 grid((a.W + kTile - 1) / kTile, (a.H + kTile - 1) / kTile);
-  phase_kernel<kHalf><<<grid, kThreads, 0, s>>>(a);
+  phase_kernel<kHalf, kMode><<<grid, kThreads, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
+template <int kMode>
+int launch_phase_m(const PhaseArgs& a, cudaStream_t s) {
+  return a.img_half ? launch_phase_t<true, kMode>(a, s) : launch_phase_t<false, kMode>(a, s);
+}
+// the method, or one of the ablations of Sec. 4 (a.ablation: bit 0 symmetric
+// propagation, bit 1 heuristic view selection)
 int launch_phase(const PhaseArgs& a, cudaStream_t s) {
-  return a.img_half ? launch_phase_t<true>(a, s) : launch_phase_t<false>(a, s);
+  switch (a.ablation & 3) {
+    case kSymmetric: return launch_phase_m<kSymmetric>(a, s);
+    case kHeuristic: return launch_phase_m<kHeuristic>(a, s);
+    case kSymmetric | kHeuristic: return launch_phase_m<kSymmetric | kHeuristic>(a, s);
+    default: return launch_phase_m<0>(a, s);
+  }
 }
 
 }  // namespace amh

@@ -73,8 +73,11 @@ __host__ __device__ constexpr float tex_scale() { return kHalf ? 1.f : 255.f; }
 template <bool kHalf, class A>
 __device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin& rw) {
   const float Ic = ref_at<kHalf, A>(a, (size_t)y * a.W + x);
+  // w = exp(-e) relative to the largest weight: the statistics of Eq. (8) are
+  // ratios of weighted sums, so the common factor cancels, and no weight
+  // underflows (squared 8-bit differences reach e = 3600)
   float rv[kWinS], wv[kWinS];
-  float sw = 0.f, s1 = 0.f;
+  float emin = 3.4e38f;
 #pragma unroll
   for (int k = 0; k < kWinS; k++) {
     const int du = -kWinR + kWinStride * (k % kWinN), dv = -kWinR + kWinStride * (k / kWinN);
@@ -82,11 +85,18 @@ __device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin
     const float r = ref_at<kHalf, A>(a, (size_t)yr * a.W + xr) - Ic;   // exact
     float dI = fabsf(r), dx = sqrtf((float)(du * du + dv * dv));
     if (a.squared) { dI = r * r; dx = (float)(du * du + dv * dv); }
-    const float w = expf(-dI * a.wI - dx * a.wX);
+    const float e = fmaf(dI, a.wI, dx * a.wX);
     rv[k] = r;
+    wv[k] = e;
+    emin = fminf(emin, e);
+  }
+  float sw = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < kWinS; k++) {
+    const float w = expf(emin - wv[k]);
     wv[k] = w;
     sw += w;
-    s1 = fmaf(w, r, s1);
+    s1 = fmaf(w, rv[k], s1);
   }
   const float inv = 1.f / sw;
   const float mr = s1 * inv;
@@ -325,10 +335,36 @@ __device__ __forceinline__ void joint_view_selection(const A& a, PixelArrays& sm
 }
 
 
+// mean of the k smallest of m[0..N), summed in ascending order (ties: lower
+// index) -- the heuristic view selection of Sec. 2
+__device__ __forceinline__ float kbest_mean(const float* m, int N, int k) {
+  uint32_t used = 0;
+  float acc = 0.f;
+  for (int r = 0; r < k; r++) {
+    int bj = -1;
+    float bmv = 0.f;
+    for (int j = 0; j < N; j++) {
+      const float mj = m[j];
+      if (!(used >> j & 1u) && (bj < 0 || mj < bmv)) { bj = j; bmv = mj; }
+    }
+    used |= 1u << bj;
+    acc += bmv;
+  }
+  return acc / (float)k;
+}
+
+// Ablations of Sec. 4 (template bits of update_pixel): kSymmetric -- each of
+// the 8 regions is one fixed candidate, the axis neighbour at distance 1
+// (regions 0-3) or 5 (regions 4-7) up, down, left, right, instead of the
+// lowest-cost pick of ACP; kHeuristic -- every hypothesis (rows, own plane,
+// refinement candidates) is scored by the mean of its own k smallest
+// per-view costs instead of MHJ, and no S_t / v_t is kept.
+constexpr int kSymmetric = 1, kHeuristic = 2;
+
 // ---------------------------------------------------------------------------
 // one pixel's checkerboard update
 // ---------------------------------------------------------------------------
-template <bool kHalf, class A>
+template <bool kHalf, int kMode = 0, class A>
 __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x, int y,
                                              int* npairs) {
   const int N = a.N;
@@ -341,14 +377,20 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 #pragma unroll
   for (int g = 0; g < kRegions; g++) {
     int best = -1;
-    float bc = 0.f;
+    if (kMode & kSymmetric) {
+      const int dist = g < 4 ? 1 : 5, dir = g & 3;
+      const int qx = x + (dir == 2 ? -dist : dir == 3 ? dist : 0), qy = y + (dir == 0 ? -dist : dir == 1 ? dist : 0);
+      if (qx >= 0 && qy >= 0 && qx < a.W && qy < a.H) best = qy * a.W + qx;
+    } else {
+      float bc = 0.f;
 #pragma unroll
-    for (int c = acp_start(g); c < acp_start(g + 1); c++) {
-      const int qx = x + acp_dx(c), qy = y + acp_dy(c);
-      if (qx < 0 || qy < 0 || qx >= a.W || qy >= a.H) continue;
-      const int q = qy * a.W + qx;
-      const float cq = __ldg(&a.cost[q]);
-      if (best < 0 || cq < bc) { best = q; bc = cq; }
+      for (int c = acp_start(g); c < acp_start(g + 1); c++) {
+        const int qx = x + acp_dx(c), qy = y + acp_dy(c);
+        if (qx < 0 || qy < 0 || qx >= a.W || qy >= a.H) continue;
+        const int q = qy * a.W + qx;
+        const float cq = __ldg(&a.cost[q]);
+        if (best < 0 || cq < bc) { best = q; bc = cq; }
+      }
     }
     pick[g] = best;
   }
@@ -389,6 +431,51 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
       const float3 c = ok ? make_float3(sm.cc(g, 0), sm.cc(g, 1), sm.cc(g, 2)) : make_float3(0.f, 0.f, 0.f);
       sm.m(g, j, N) = ncc_cost<kHalf>(V, c, ok, fx, fy, rw, npairs);
     }
+  }
+
+  if (kMode & kHeuristic) {
+    const int k = a.k < N ? a.k : N;
+    float4 best = a.plane[pi];
+    float3 c;
+    bool ok = plane_c(a.Kinv, best, ray, &c);
+    for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs);
+    float bm = kbest_mean(sm.w, N, k);
+    int choice = 8;
+    float bestD = 0.f;
+#pragma unroll 1
+    for (int g = 0; g < kRegions; g++) {
+      if (!(valid >> g & 1u)) continue;
+      const float r = kbest_mean(&sm.M[g * kMaxSrc], N, k);
+      if (r < bm) { bm = r; choice = g; }
+    }
+    if (choice < 8) {
+#pragma unroll
+      for (int g = 0; g < kRegions; g++) if (g == choice) bestD = hD[g];
+      const float4 pq = a.plane[pick[choice]];
+      best = make_float4(pq.x, pq.y, pq.z, bestD);
+    }
+    const int nc = a.t < 3 ? 1 : kMaxRefine;
+    int bc = -1;
+    float bcm = 0.f;
+#pragma unroll 1
+    for (int ci = 0; ci < nc; ci++) {
+      ok = plane_c(a.Kinv, refine_candidate(a, x, y, best, ray, ci), ray, &c);
+      for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs);
+      const float m = kbest_mean(sm.w, N, k);
+      if (bc < 0 || m < bcm) { bc = ci; bcm = m; }
+    }
+    if (bc >= 0 && bcm < bm) {
+      bm = bcm;
+      best = refine_candidate(a, x, y, best, ray, bc);
+      choice = 9 + bc;
+    }
+    a.plane[pi] = best;
+    a.cost[pi] = bm;
+    a.sel[pi] = 0;
+    a.vbest[pi] = 255;
+    a.wmask[pi] = 0;
+    a.choice[pi] = (uint8_t)choice;
+    return;
   }
 
   // --- Eqs. (2)-(6) ------------------------------------------------------------------

@@ -193,3 +193,31 @@ def test_fp16_and_uint8_agree_on_integer_images(amh, tiny_scene):
     sa, sb = a.get_state(), b.get_state()
     assert (np.abs(sa["cost"] - sb["cost"]) <= COST_TOL).mean() >= FRACTION
     assert same_plane(sa["plane"].astype(np.float64), sb["plane"].astype(np.float64), 1e-4, 1e-6).mean() >= 0.995
+
+
+@pytest.mark.parametrize("flags", ["squared", "symmetric", "heuristic", "symmetric+heuristic"])
+@pytest.mark.parametrize("t", [1, 4])
+def test_phase_parity_flags(oracle_mod, amh, tiny_scene, flags, t):
+    """The parameter flags -- squared bilateral differences and the two
+    ablations of Sec. 4 -- on both sides, one phase from identical state."""
+    f = {"squared": 1, "symmetric": 4, "heuristic": 8, "symmetric+heuristic": 12}[flags]
+    sc = tiny_scene
+    o, g = _pair(oracle_mod, amh, sc, seed=60 + t, flags=f)
+    assert g.params.flags == f
+    o.init_random()
+    o.iterate(min(t, 2))
+    st = o.get_state()
+    st["t"] = t
+    for color in (0, 1):
+        r = phase_check(o, g, st, color)
+        assert r["frac_ok_nontie"] >= FRACTION, r
+        assert r["frac_sel"] >= FRACTION and r["frac_v"] >= FRACTION, r
+    if f & 8:
+        assert (g.get_state()["vbest"] == 255).all()
+
+
+def test_ablations_rejected_by_the_batch(amh, tiny_scene):
+    sc = tiny_scene
+    p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=amh.AMH_FLAG_HEURISTIC_VIEWS)
+    with pytest.raises(amh.AmhError):
+        amh.Batch(sc.cams, sc.images, [sc.ref], [sc.src], p)
