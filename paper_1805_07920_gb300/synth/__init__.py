@@ -196,6 +196,24 @@ def scene_tiny(seed=1):
     return Scene("tiny", seed, cams, imgs, ref, src, 2.0, 8.0, gd, gn)
 
 
+def scene_fusion(seed=6, n=5):
+    """The tiny scene's two slanted planes seen by n cameras on a 20-degree
+    arc, with ground-truth depth and normals for every view (depth-map fusion
+    tests)."""
+    W, H, f = 160, 120, 150.0
+    cams = _arc_cams(n, W, H, f, radius=4.0, arc_deg=20.0)
+    tf = _tex_freq(4.0, f)
+    prims = [
+        _prim(SYN_QUAD, a=(-0.9, 0, -0.3), b=(1.2 * math.cos(0.52), 0, 1.2 * math.sin(0.52)),
+              c=(0, 2.5, 0), albedo=0.5, tex_freq=tf, tex_off=3.1),
+        _prim(SYN_PLANE, a=(0, math.sin(0.44), -math.cos(0.44)), b=(1.2, 0, 0), albedo=0.5,
+              tex_freq=tf, tex_off=11.7),
+    ]
+    ref, src = _centre_first(n)
+    imgs, gd, gn = render(cams, prims, seed, gt_views=tuple(range(n)))
+    return Scene("fusion", seed, cams, imgs, ref, src, 2.0, 8.0, gd, gn)
+
+
 def scene_medium(seed=2):
     W, H, f = 640, 480, 560.0
     cams = _arc_cams(6, W, H, f, radius=6.0, arc_deg=40.0, height_off=-0.8)
@@ -305,7 +323,7 @@ def ring_sources(ref, n=20, n_src=10):
 
 
 SCENES = {"tiny": scene_tiny, "medium": scene_medium, "large": scene_large,
-          "ring20": scene_ring20, "learned": scene_learned}
+          "ring20": scene_ring20, "learned": scene_learned, "fusion": scene_fusion}
 
 
 def make_scene(name: str, seed: int | None = None, cache_dir: str | None = None) -> Scene:
