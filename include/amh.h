@@ -328,6 +328,35 @@ AMH_API void amh_net_destroy(amh_net* net);
 AMH_API int amh_read_maps_noalloc(amh_ctx* ctx, float* depth, float* normal3,
                                   int64_t first_pixel, int64_t n_pixels);
 
+/* ------------------------------------------------------------------------
+ * Post-processing of depth maps (Sec. 3.3, last two paragraphs; the details
+ * follow Gipuma, the paper's reference [9], under these readings).  Both
+ * calls take DEVICE buffers the caller owns and run asynchronously on
+ * `stream`; errors: AMH_EINVAL for NULL / aliased buffers or bad sizes,
+ * AMH_ECUDA for a failed launch.
+ * ------------------------------------------------------------------------ */
+/* 4x4 median of a width x height depth map: the window holds the offsets
+ * -2..+1 in x and y (clamped at the borders), the value is the mean of its
+ * 8th and 9th smallest entries (exact to FP32 rounding).  depth_in and
+ * depth_out must differ. */
+AMH_API int amh_median4(const float* depth_in, float* depth_out, int32_t width, int32_t height, void* stream);
+/* Consistency fusion of n_views (2..32) depth maps: depth[v] (W_v x H_v
+ * z-depths, <= 0 = none) and normal3[v] (W_v x H_v x 3, view v's camera
+ * coordinates) of camera cams[v] (host array of device pointers).  Pixel p of
+ * view i back-projects to the world point X with world normal n; view j
+ * agrees when X lies in front of it and projects to the pixel q = (floor(u +
+ * 0.5), floor(v + 0.5)) inside it with depth D_j(q) > 0, the disparity
+ * difference f_j |C_i - C_j| |1/z_j(X) - 1/D_j(q)| (f_j = K_j[0], C the camera
+ * centres, z_j(X) the depth of X in view j) is at most f_eps, and the angle
+ * between n and view j's normal at q is at most f_ang_deg.  count[v] (W_v x
+ * H_v uint8) receives the number of agreeing views; where it reaches f_con,
+ * points6[v] (W_v x H_v x 6 floats) receives the mean of X and the agreeing
+ * views' back-projected points and the normalised sum of the normals (world
+ * coordinates), else zeros.  The paper fixes f_eps 0.3, f_ang 30, f_con 2. */
+AMH_API int amh_fuse(int32_t n_views, const amh_camera* cams, const float* const* depth,
+                     const float* const* normal3, float f_eps, float f_ang_deg, int32_t f_con,
+                     float* const* points6, uint8_t* const* count, void* stream);
+
 /* The texture-gather ceiling of the current GPU, measured (this project's
  * measurement utility, not part of the method): a loop of nothing but 2x2
  * gathers of a uint8 texture laid out like the update's windows, 16 warps per

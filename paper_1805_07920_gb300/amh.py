@@ -33,7 +33,7 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
            "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
            "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
-           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak"]
+           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse"]
 
 
 class AmhError(RuntimeError):
@@ -106,6 +106,47 @@ def gather_peak() -> float:
     if rc != AMH_OK:
         raise AmhError(rc, "gather peak measurement failed")
     return v.value
+
+
+def median4(depth):
+    """4x4 median of a depth map (torch float32 CUDA tensor, H x W) into a new
+    tensor, on the current stream (``amh_median4``)."""
+    import torch
+    d = depth.contiguous()
+    out = torch.empty_like(d)
+    L = lib()
+    L.amh_median4.argtypes = [_vp, _vp, _i32, _i32, _vp]
+    rc = L.amh_median4(_vp(d.data_ptr()), _vp(out.data_ptr()), d.shape[1], d.shape[0], _current_stream())
+    if rc != AMH_OK:
+        raise AmhError(rc, "amh_median4 failed")
+    return out
+
+
+def fuse(cams, depths, normals, f_eps=0.3, f_ang_deg=30.0, f_con=2):
+    """Consistency fusion (``amh_fuse``) of per-view depth (H x W) and normal
+    (H x W x 3, camera coordinates) torch float32 CUDA tensors; returns
+    (points (H x W x 6 world coordinates and normal) and counts (H x W uint8))
+    per view."""
+    import torch
+    V = len(cams)
+    arr = make_cameras(cams)
+    d = [x.contiguous() for x in depths]
+    n = [x.contiguous() for x in normals]
+    pts = [torch.zeros(x.shape[0], x.shape[1], 6, dtype=torch.float32, device=x.device) for x in d]
+    cnt = [torch.zeros(x.shape[0], x.shape[1], dtype=torch.uint8, device=x.device) for x in d]
+    keep = []
+
+    def P(ts):
+        a = (_vp * V)(*[_vp(t.data_ptr()) for t in ts])
+        keep.append(a)
+        return ctypes.cast(a, _vp)
+
+    L = lib()
+    L.amh_fuse.argtypes = [_i32, ctypes.POINTER(Camera), _vp, _vp, ctypes.c_float, ctypes.c_float, _i32, _vp, _vp, _vp]
+    rc = L.amh_fuse(V, arr, P(d), P(n), float(f_eps), float(f_ang_deg), int(f_con), P(pts), P(cnt), _current_stream())
+    if rc != AMH_OK:
+        raise AmhError(rc, "amh_fuse failed")
+    return pts, cnt
 
 
 def default_params(**kw) -> Params:
