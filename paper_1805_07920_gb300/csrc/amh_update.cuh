@@ -538,14 +538,25 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   const int ncand = nc + (has_prop ? 1 : 0);
   int bc = -1;
   float bcm = 0.f;
+  // A candidate can only change the outcome if its cost ends strictly below
+  // both the current best and the best candidate so far.  Its weighted sum
+  // only grows view by view (w_j >= 0, m_j >= 0, and rounding is monotone),
+  // so once sum * inv_sw reaches that bound it has lost: its remaining views
+  // are skipped, and the result is exactly that of the full evaluation.
 #pragma unroll 1
   for (int ci = 0; ci < ncand; ci++) {
     ok = plane_c(a.Kinv, ci < nc ? refine_candidate(a, x, y, best, ray, ci) : prop, ray, &c);
+    const float bound = bc < 0 ? bm : fminf(bm, bcm);
     float m = 0.f;
-    for (int j = 0; j < N; j++) {
+    bool alive = true;
+    for (int j = 0; j < N; j++) {   // j stays warp-uniform (one texture per gather)
       const float wj = sm.wt(j);
-      if (wj > 0.f) m = fmaf(wj, ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs), m);
+      if (wj > 0.f && alive) {
+        m = fmaf(wj, ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs), m);
+        alive = m * inv_sw < bound;
+      }
     }
+    if (!alive) continue;
     m *= inv_sw;
     if (bc < 0 || m < bcm) { bc = ci; bcm = m; }
   }
