@@ -357,6 +357,20 @@ AMH_API int amh_fuse(int32_t n_views, const amh_camera* cams, const float* const
                      const float* const* normal3, float f_eps, float f_ang_deg, int32_t f_con,
                      float* const* points6, uint8_t* const* count, void* stream);
 
+/* Source-view preselection (Sec. 2 / Sec. 4: the N source views are chosen
+ * "according to viewing angle and baseline"; host-only, no GPU needed).
+ * Reading: P is the point at z-depth `depth` on the reference's optical
+ * axis; a view qualifies when P lies in front of it and projects inside its
+ * image, and the triangulation angle between the rays from P to the two
+ * camera centres lies in [min_angle_deg, max_angle_deg] (the lower bound asks
+ * for baseline, the upper for similar appearance).  Qualifying views are
+ * ranked by increasing angle (ties: lower index); the first n_src go to
+ * src_out (capacity n_src), their number to *n_out.  AMH_EINVAL for a bad
+ * reference, non-positive depth, n_src < 1 or an empty angle range. */
+AMH_API int amh_select_sources(int32_t n_views, const amh_camera* cams, int32_t ref, double depth,
+                               int32_t n_src, double min_angle_deg, double max_angle_deg,
+                               int32_t* src_out, int32_t* n_out);
+
 /* The texture-gather ceiling of the current GPU, measured (this project's
  * measurement utility, not part of the method): a loop of nothing but 2x2
  * gathers of a uint8 texture laid out like the update's windows, 16 warps per

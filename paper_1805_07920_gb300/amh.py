@@ -33,7 +33,7 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
            "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
            "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
-           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse"]
+           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse", "amh_select_sources"]
 
 
 class AmhError(RuntimeError):
@@ -95,6 +95,21 @@ def lib():
         L.amh_destroy.restype = None
         _LIB = L
     return _LIB
+
+
+def select_sources(cams, ref, depth, n_src=10, min_angle_deg=1.0, max_angle_deg=60.0):
+    """Source views for reference `ref` by triangulation angle at the point at
+    z-depth `depth` on its optical axis (``amh_select_sources``)."""
+    L = lib()
+    L.amh_select_sources.argtypes = [_i32, ctypes.POINTER(Camera), _i32, ctypes.c_double, _i32, ctypes.c_double,
+                                     ctypes.c_double, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+    out = (_i32 * int(n_src))()
+    n = _i32()
+    rc = L.amh_select_sources(len(cams), make_cameras(cams), int(ref), float(depth), int(n_src),
+                              float(min_angle_deg), float(max_angle_deg), out, ctypes.byref(n))
+    if rc != AMH_OK:
+        raise AmhError(rc, L.amh_last_error(None).decode())
+    return [int(out[i]) for i in range(n.value)]
 
 
 def gather_peak() -> float:

@@ -4,12 +4,14 @@
 // runs in those kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "amh.h"
 #include "amh_device.cuh"
@@ -281,6 +283,50 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   CTRY(cudaStreamSynchronize(c->stream));
 #undef CTRY
   *out = c;
+  return AMH_OK;
+}
+
+AMH_API int amh_select_sources(int32_t n_views, const amh_camera* cams, int32_t ref, double depth,
+                               int32_t n_src, double min_angle_deg, double max_angle_deg,
+                               int32_t* src_out, int32_t* n_out) {
+  if (!cams || !src_out || !n_out || n_views < 2 || ref < 0 || ref >= n_views || !(depth > 0) || n_src < 1 ||
+      !(min_angle_deg >= 0) || !(max_angle_deg >= min_angle_deg))
+    return fail(nullptr, AMH_EINVAL, "invalid source-selection arguments");
+  if (!camera_ok(cams[ref])) return fail(nullptr, AMH_EINVAL, "reference camera invalid");
+  const amh_camera& cr = cams[ref];
+  auto centre = [](const amh_camera& c, double C[3]) {   // -R^T t
+    for (int r = 0; r < 3; r++) C[r] = -(c.R[r] * c.t[0] + c.R[3 + r] * c.t[1] + c.R[6 + r] * c.t[2]);
+  };
+  double Cr[3], P[3];
+  centre(cr, Cr);
+  // optical axis in world coordinates: the third row of R
+  for (int r = 0; r < 3; r++) P[r] = Cr[r] + depth * cr.R[6 + r];
+  std::vector<std::pair<double, int>> cand;
+  for (int v = 0; v < n_views; v++) {
+    if (v == ref || !camera_ok(cams[v])) continue;
+    const amh_camera& c = cams[v];
+    double Xc[3];
+    for (int r = 0; r < 3; r++) Xc[r] = c.R[3 * r] * P[0] + c.R[3 * r + 1] * P[1] + c.R[3 * r + 2] * P[2] + c.t[r];
+    if (!(Xc[2] > 0)) continue;
+    const double u = (c.K[0] * Xc[0] + c.K[1] * Xc[1] + c.K[2] * Xc[2]) / Xc[2];
+    const double w = (c.K[3] * Xc[0] + c.K[4] * Xc[1] + c.K[5] * Xc[2]) / Xc[2];
+    if (!(u >= 0 && u <= c.width - 1 && w >= 0 && w <= c.height - 1)) continue;
+    double Cv[3], a[3], b[3];
+    centre(c, Cv);
+    for (int r = 0; r < 3; r++) { a[r] = Cr[r] - P[r]; b[r] = Cv[r] - P[r]; }
+    const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double nb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    if (!(na > 0 && nb > 0)) continue;
+    const double cosang = std::max(-1.0, std::min(1.0, (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (na * nb)));
+    const double ang = std::acos(cosang) * 180.0 / 3.14159265358979323846;
+    if (ang >= min_angle_deg && ang <= max_angle_deg) cand.push_back({ang, v});
+  }
+  std::stable_sort(cand.begin(), cand.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first < y.first || (x.first == y.first && x.second < y.second);
+  });
+  const int n = std::min<int>(n_src, (int)cand.size());
+  for (int i = 0; i < n; i++) src_out[i] = cand[i].second;
+  *n_out = n;
   return AMH_OK;
 }
 
