@@ -19,6 +19,7 @@ NREGION = 8
 ORC_FLAG_SQUARED = 1        # squared differences in the bilateral weight
 ORC_FLAG_SYMMETRIC = 4      # ablation: symmetric checkerboard propagation
 ORC_FLAG_HEURISTIC = 8      # ablation: heuristic (per-hypothesis k-best) view selection
+ORC_FLAG_TEXTURE_BILINEAR = 16  # bilinear weights as a texture unit's linear filter forms them
 
 
 def build_command() -> list[str]:
@@ -85,6 +86,8 @@ def lib():
         L.orc_homography.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp]
         L.orc_bilinear.restype = ctypes.c_double
         L.orc_bilinear.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_bilinear_texture.restype = ctypes.c_double
+        L.orc_bilinear_texture.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.orc_cost.restype = ctypes.c_double
         L.orc_cost.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]
         L.orc_mhj.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int, _vp, _vp, ctypes.c_int,
@@ -143,6 +146,11 @@ def confidence(m: float, params: OrcParams | None = None) -> float:
 def bilinear(img: np.ndarray, x: float, y: float) -> float:
     a = np.ascontiguousarray(img, np.float64)
     return lib().orc_bilinear(_ptr(a), a.shape[1], a.shape[0], x, y)
+
+
+def bilinear_texture(img: np.ndarray, x: float, y: float) -> float:
+    a = np.ascontiguousarray(img, np.float64)
+    return lib().orc_bilinear_texture(_ptr(a), a.shape[1], a.shape[0], x, y)
 
 
 def acp_offsets(g: int):

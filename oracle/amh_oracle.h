@@ -57,11 +57,14 @@ typedef struct {
   int flags;                 /* bit 0: squared bilateral differences;
                                 bit 2: symmetric propagation (ablation
                                 "\\ACP" of Sec. 4); bit 3: heuristic view
-                                selection (ablation "\\MHJ" of Sec. 4)       */
+                                selection (ablation "\\MHJ" of Sec. 4);
+                                bit 4: texture-unit bilinear interpolation
+                                (orc_bilinear_texture)                      */
 } orc_params;
 
 #define ORC_FLAG_SYMMETRIC 4
 #define ORC_FLAG_HEURISTIC 8
+#define ORC_FLAG_TEXTURE_BILINEAR 16
 
 typedef struct orc_ctx orc_ctx;
 
@@ -105,6 +108,7 @@ double orc_confidence(const orc_params* p, double m);
 /* plane-induced homography of source view j (index into src[]) */
 void   orc_homography(const orc_ctx* c, int j, const double n[3], double d, double H[9]);
 double orc_bilinear(const double* img, int W, int H, double x, double y);
+double orc_bilinear_texture(const double* img, int W, int H, double x, double y);
 /* matching cost m of one plane (n, D at pixel x) against source view j (Eq. 8) */
 double orc_cost(const orc_ctx* c, int x, int y, const double plane[4], int j);
 /* multi-hypothesis joint view selection on an 8 x N matrix (Eqs. 2-6) */

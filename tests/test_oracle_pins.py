@@ -132,6 +132,70 @@ def test_bilinear_clamps_to_edge(oracle_mod):
     assert oracle_mod.bilinear(img, 1.5, 10.0) == pytest.approx(0.5 * (img[3, 1] + img[3, 2]))
 
 
+def _textbook(img, x, y):
+    """Bilinear value from the four product weights (a different form of the
+    interpolation than the oracle's lerps)."""
+    x0, y0 = int(np.floor(x)), int(np.floor(y))
+    fx, fy = x - x0, y - y0
+    return ((1 - fx) * (1 - fy) * img[y0, x0] + fx * (1 - fy) * img[y0, x0 + 1]
+            + (1 - fx) * fy * img[y0 + 1, x0] + fx * fy * img[y0 + 1, x0 + 1])
+
+
+def test_texture_bilinear_on_the_weight_grid(oracle_mod):
+    """Fractions k/16 put alpha, beta and alpha * beta on the 1/256 grid: the
+    texture form is then the plain bilinear value."""
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, (6, 7)).astype(np.float64)
+    for _ in range(300):
+        x = rng.integers(0, 5) + rng.integers(0, 16) / 16.0
+        y = rng.integers(0, 4) + rng.integers(0, 16) / 16.0
+        assert oracle_mod.bilinear_texture(img, x, y) == pytest.approx(_textbook(img, x, y), abs=1e-12)
+        assert oracle_mod.bilinear_texture(img, x, y) == pytest.approx(oracle_mod.bilinear(img, x, y), abs=1e-12)
+
+
+def test_texture_bilinear_rounding_rules(oracle_mod):
+    row = np.array([[0.0, 256.0], [0.0, 256.0]])
+    # fractions rounded half up to 1/256
+    assert oracle_mod.bilinear_texture(row, 0.5 / 256, 0.0) == 1.0
+    assert oracle_mod.bilinear_texture(row, 0.49 / 256, 0.0) == 0.0
+    assert oracle_mod.bilinear_texture(row, 1.49 / 256, 0.0) == 1.0
+    assert oracle_mod.bilinear_texture(row, 255.5 / 256, 0.0) == 256.0
+    # the cross term is alpha * beta rounded to 1/256: 24/256 * 40/256 = 3.75/256 -> 4/256
+    corner = np.array([[0.0, 0.0], [0.0, 256.0]])
+    assert oracle_mod.bilinear_texture(corner, 24 / 256, 40 / 256) == 4.0
+    assert _textbook(corner, 24 / 256, 40 / 256) == pytest.approx(3.75)
+    # 8/256 * 48/256 = 1.5/256: a tie, rounded up
+    assert oracle_mod.bilinear_texture(corner, 8 / 256, 48 / 256) == 2.0
+    # affine images have no cross term: the value is exact at the rounded position
+    yy, xx = np.mgrid[0:4, 0:5]
+    ramp = 7.0 + 2.0 * xx + 5.0 * yy
+    assert oracle_mod.bilinear_texture(ramp, 1 + 10.3 / 256, 2 + 99.7 / 256) == pytest.approx(
+        7.0 + 2.0 * (1 + 10 / 256) + 5.0 * (2 + 100 / 256), abs=1e-12)
+
+
+def test_texture_bilinear_error_bound_and_clamping(oracle_mod):
+    rng = np.random.default_rng(4)
+    img = rng.integers(0, 256, (8, 9)).astype(np.float64)
+    worst = 0.0
+    for _ in range(2000):
+        x, y = rng.uniform(0, 8), rng.uniform(0, 7)
+        x0, y0 = int(np.floor(x)), int(np.floor(y))
+        if x0 >= 8 or y0 >= 7:
+            continue
+        a, b, c, d = img[y0, x0], img[y0, x0 + 1], img[y0 + 1, x0], img[y0 + 1, x0 + 1]
+        bound = (abs(b - a) + abs(c - a) + 3 * abs(d - b - c + a)) / 512
+        err = abs(oracle_mod.bilinear_texture(img, x, y) - _textbook(img, x, y))
+        assert err <= bound + 1e-12
+        worst = max(worst, err / max(bound, 1e-12))
+    assert worst > 0.3          # the rounding is visible, not a no-op
+    # outside the image the edge texels repeat (clamp-to-edge addressing)
+    for x, y in ((1.5, 10.0), (-0.3, 2.75), (12.0, 3.25)):
+        assert oracle_mod.bilinear_texture(img, x, y) == oracle_mod.bilinear_texture(
+            img, min(max(x, 0.0), 8.0), min(max(y, 0.0), 7.0))
+    assert oracle_mod.bilinear_texture(img, -3.0, -7.0) == img[0, 0]
+    assert oracle_mod.bilinear_texture(img, 9.0, 1.0) == img[1, 8]
+
+
 # --------------------------------------------------------------------------
 # geometry: plane-induced homography
 # --------------------------------------------------------------------------
