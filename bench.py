@@ -354,6 +354,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and world == 1:     # one-GPU measurements of the other forms
+        extras["texture_bilinear_3200x2112"] = bench_texture(sc, args.steps, phase_ms, ctx)
         extras["batched_ring20"] = bench_batch(args, dist)
         extras["learned_proposal_1600x1056"] = bench_learned()
 
@@ -381,6 +382,53 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def bench_texture(sc, steps, default_phase_ms, default_ctx):
+    """The same workload in the texture-filter precision form
+    (AMH_FLAG_TEXTURE_BILINEAR): throughput, phase-launch time, and the
+    fraction of pixels within 1 % of the ground truth next to the default
+    form's (both after the last timed step)."""
+    import torch
+    from paper_1805_07920_gb300 import amh
+    ctx = amh.Context.from_scene(sc, seed=SEED, flags=amh.AMH_FLAG_TEXTURE_BILINEAR)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        ctx.init_random()
+        ctx.iterate(ITERS)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ph = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps * 2 * ITERS)]
+    ev0.record(stream)
+    k = 0
+    for _ in range(steps):
+        ctx.init_random()
+        for _it in range(ITERS):
+            for color in (0, 1):
+                ph[k][0].record(stream)
+                ctx.step_phase(color)
+                ph[k][1].record(stream)
+                k += 1
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    phase_ms = float(np.mean([a.elapsed_time(b) for a, b in ph]))
+    gt = sc.gt_depth[sc.ref].astype(np.float64)
+    m = gt > 0
+    m[:5] = m[-5:] = False
+    m[:, :5] = m[:, -5:] = False
+
+    def acc(c):
+        d = c.read_maps()["depth"].astype(np.float64)
+        return round(float((np.abs(d - gt)[m] <= 0.01 * gt[m]).mean()), 4)
+    out = {"metric": METRIC, "unit": UNIT, "value": round(job_rate(sc.width * sc.height, ITERS, steps, 1, ms), 3),
+           "ms_per_step": round(ms / steps, 3), "launch_ms": round(phase_ms, 3),
+           "launch_ms_default_form": round(default_phase_ms, 3),
+           "accuracy_1pct": acc(ctx), "accuracy_1pct_default_form": acc(default_ctx),
+           "interpolation": "texture-unit linear filter (fractions and their product rounded to 1/256)"}
+    ctx.close()
+    return out
 
 
 def bench_batch(args, dist):

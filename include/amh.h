@@ -73,10 +73,17 @@ enum {
                                      is one fixed candidate, the axis
                                      neighbour at distance 1 (g = 0..3) or 5
                                      (g = 4..7) up / down / left / right    */
-  AMH_FLAG_HEURISTIC_VIEWS = 8    /* instead of MHJ (Sec. 3.2): every
+  AMH_FLAG_HEURISTIC_VIEWS = 8,   /* instead of MHJ (Sec. 3.2): every
                                      hypothesis is scored by the mean of its
                                      own k smallest per-view costs; no S_t or
                                      v_t is kept (sel 0, vbest 255)           */
+  /* Precision form of the warped samples of Eq. (8) (the paper does not fix
+   * the interpolation): the texture unit's linear filter interpolates, with
+   * its fractions and their product rounded half up to 1/256, instead of
+   * FP32 blends of gathered texels (fewer instructions per sample).  uint8
+   * images and the method's own propagation / view selection only; single
+   * contexts only (amh_create / amh_batch_create reject other combinations). */
+  AMH_FLAG_TEXTURE_BILINEAR = 16
 };
 
 typedef struct amh_ctx amh_ctx;

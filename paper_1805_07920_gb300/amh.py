@@ -21,6 +21,7 @@ AMH_FLAG_BILATERAL_SQUARED = 1
 AMH_FLAG_SYMMETRIC_PROPAGATION = 4   # ablation: symmetric checkerboard propagation
 AMH_FLAG_HEURISTIC_VIEWS = 8         # ablation: per-hypothesis k-best view selection
 AMH_FLAG_IMAGES_F16 = 2
+AMH_FLAG_TEXTURE_BILINEAR = 16       # precision form: texture-unit bilinear interpolation
 MAX_SRC = 32
 NOALLOC_MAX_PIXELS = 262144
 

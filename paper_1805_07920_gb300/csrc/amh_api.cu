@@ -151,6 +151,9 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   if (!(p->k >= 1) || p->n1 < 0 || p->n2 < 0 || !(p->beta > 0) || !(p->sigma_I > 0) || !(p->sigma_x > 0) ||
       !(p->alpha > 0) || !(p->depth_min > 0) || !(p->depth_max > p->depth_min))
     return fail(nullptr, AMH_EINVAL, "invalid parameters");
+  if ((p->flags & AMH_FLAG_TEXTURE_BILINEAR) &&
+      (p->flags & (AMH_FLAG_IMAGES_F16 | AMH_FLAG_SYMMETRIC_PROPAGATION | AMH_FLAG_HEURISTIC_VIEWS)))
+    return fail(nullptr, AMH_EINVAL, "AMH_FLAG_TEXTURE_BILINEAR takes uint8 images and the method's own propagation and view selection");
   for (int j = 0; j < n_src; j++) {
     const int v = src[j];
     if (v < 0 || v >= n_views || v == ref) return fail(nullptr, AMH_EINVAL, "src[%d] = %d invalid", j, v);
@@ -223,6 +226,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   a.squared = (p->flags & AMH_FLAG_BILATERAL_SQUARED) ? 1 : 0;
   a.img_half = half ? 1 : 0;
   a.ablation = ((p->flags & AMH_FLAG_SYMMETRIC_PROPAGATION) ? 1 : 0) | ((p->flags & AMH_FLAG_HEURISTIC_VIEWS) ? 2 : 0);
+  a.tex_filter = (p->flags & AMH_FLAG_TEXTURE_BILINEAR) ? 1 : 0;
   a.dmin = p->depth_min;
   a.dmax = p->depth_max;
   a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
@@ -260,8 +264,9 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     for (int i = 0; i < 3; i++) V.b[i] = (float)b[i];
     V.xmax = (float)cj.width;
     V.ymax = (float)cj.height;
-    // the view as a texture: point sampling, clamp to edge; uint8 read as
-    // value / 255, FP16 read as the value
+    // the view as a texture: clamp to edge; uint8 read as value / 255, FP16
+    // read as the value; point sampling (the kernels gather 2 x 2 texels and
+    // blend in FP32) or, for AMH_FLAG_TEXTURE_BILINEAR, the linear filter
     cudaChannelFormatDesc fd = half ? cudaCreateChannelDescHalf() : cudaCreateChannelDesc<uint8_t>();
     CTRY(cudaMallocArray(&c->arr[j], &fd, cj.width, cj.height, cudaArrayTextureGather));
     CTRY(cudaMemcpy2DToArrayAsync(c->arr[j], 0, 0, images[v], cj.width * es, cj.width * es, cj.height, kind,
@@ -274,7 +279,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     std::memset(&td, 0, sizeof td);
     td.addressMode[0] = cudaAddressModeClamp;
     td.addressMode[1] = cudaAddressModeClamp;
-    td.filterMode = cudaFilterModePoint;
+    td.filterMode = a.tex_filter ? cudaFilterModeLinear : cudaFilterModePoint;
     td.readMode = half ? cudaReadModeElementType : cudaReadModeNormalizedFloat;
     td.normalizedCoords = 0;
     CTRY(cudaCreateTextureObject(&c->tex[j], &rd, &td, nullptr));

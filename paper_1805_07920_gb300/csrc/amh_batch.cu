@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBThreads) batch_init_kernel(const __grid_cons
     const int x = tx * 16 + (threadIdx.x & 15), y = ty * 8 + (threadIdx.x >> 4);
     if (x < ra.W && y < ra.H) {
       PixelArrays sm;
-      init_pixel<kHalf>(ra, sm, x, y, &npairs);
+      init_pixel<kHalf, false>(ra, sm, x, y, &npairs);
     }
   }
   const int tot = __reduce_add_sync(0xffffffffu, npairs);
@@ -308,8 +308,8 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
   if (!(p->k >= 1) || p->n1 < 0 || p->n2 < 0 || !(p->beta > 0) || !(p->sigma_I > 0) || !(p->sigma_x > 0) ||
       !(p->alpha > 0) || !(p->depth_min > 0) || !(p->depth_max > p->depth_min))
     return bfail(nullptr, AMH_EINVAL, "invalid parameters");
-  if (p->flags & (AMH_FLAG_SYMMETRIC_PROPAGATION | AMH_FLAG_HEURISTIC_VIEWS))
-    return bfail(nullptr, AMH_EINVAL, "the ablation flags apply to single contexts only");
+  if (p->flags & (AMH_FLAG_SYMMETRIC_PROPAGATION | AMH_FLAG_HEURISTIC_VIEWS | AMH_FLAG_TEXTURE_BILINEAR))
+    return bfail(nullptr, AMH_EINVAL, "the ablation and texture-filter flags apply to single contexts only");
   if (src_offsets[0] != 0) return bfail(nullptr, AMH_EINVAL, "src_offsets[0] must be 0");
   for (int r = 0; r < n_refs; r++) {
     const int ref = refs[r];

@@ -46,6 +46,7 @@ struct PhaseArgs {
   int squared;               // bilateral weight on squared differences
   int img_half;              // images are FP16 (else uint8)
   int ablation;              // bit 0: symmetric propagation, bit 1: heuristic views (Sec. 4)
+  int tex_filter;            // samples through the texture unit's linear filter
   float dmin, dmax;
   uint32_t key0, key1;       // Philox key (seed)
   const void* ref;           // reference image, W x H (uint8 or FP16)

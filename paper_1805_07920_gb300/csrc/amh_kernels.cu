@@ -34,12 +34,12 @@ __global__ void __launch_bounds__(kThreads, kPhaseBlocksPerSM) phase_kernel(cons
 }
 
 // Random initialisation: one thread per pixel over the whole image.
-template <bool kHalf>
+template <bool kHalf, bool kTex>
 __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ PhaseArgs a) {
   PixelArrays sm;
   const int x = blockIdx.x * kTile + (threadIdx.x & 15), y = blockIdx.y * 8 + (threadIdx.x >> 4);
   int npairs = 0;
-  if (x < a.W && y < a.H) init_pixel<kHalf>(a, sm, x, y, &npairs);
+  if (x < a.W && y < a.H) init_pixel<kHalf, kTex>(a, sm, x, y, &npairs);
   count_pairs(a, npairs);
 }
 
@@ -52,16 +52,19 @@ void prefer_l1(K kernel) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 
-template <bool kHalf>
+template <bool kHalf, bool kTex>
 int launch_init_t(const PhaseArgs& a, cudaStream_t s) {
-  static bool once = (prefer_l1(init_kernel<kHalf>), true);
+  static bool once = (prefer_l1(init_kernel<kHalf, kTex>), true);
   (void)once;
   dim3 grid((a.W + kTile - 1) / kTile, (a.H + 7) / 8);
-  init_kernel<kHalf><<<grid, kThreads, 0, s>>>(a);
+  init_kernel<kHalf, kTex><<<grid, kThreads, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
+// the texture-filter form exists for uint8 images only (the context refuses
+// it with FP16 images and with the ablations)
 int launch_init(const PhaseArgs& a, cudaStream_t s) {
-  return a.img_half ? launch_init_t<true>(a, s) : launch_init_t<false>(a, s);
+  if (a.tex_filter) return launch_init_t<false, true>(a, s);
+  return a.img_half ? launch_init_t<true, false>(a, s) : launch_init_t<false, false>(a, s);
 }
 
 template <bool kHalf, int kMode>
@@ -79,6 +82,7 @@ int launch_phase_m(const PhaseArgs& a, cudaStream_t s) {
 // the method, or one of the ablations of Sec. 4 (a.ablation: bit 0 symmetric
 // propagation, bit 1 heuristic view selection)
 int launch_phase(const PhaseArgs& a, cudaStream_t s) {
+  if (a.tex_filter) return launch_phase_t<false, kTexture>(a, s);
   switch (a.ablation & 3) {
     case kSymmetric: return launch_phase_m<kSymmetric>(a, s);
     case kHeuristic: return launch_phase_m<kHeuristic>(a, s);

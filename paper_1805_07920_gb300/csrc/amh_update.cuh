@@ -127,7 +127,7 @@ __device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin
 // otherwise clamped to [0, 2].  Window samples outside the view are clamped to
 // its edge by the texture unit.
 // ---------------------------------------------------------------------------
-template <bool kHalf>
+template <bool kHalf, bool kTex = false>
 __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok, float x, float y,
                                           const RefWin& rw, int* evaluated) {
   if (!ok) return kWorst;
@@ -170,19 +170,30 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
       unpack2(qb, qxb, qyb);
       const float ia = rcp_approx(qz0), ib = rcp_approx(qz1);
       const f2 pa = pack2(qxa * ia, qya * ia), pb = pack2(qxb * ib, qyb * ib);
-      const f2 fla = floor2(pa), flb = floor2(pb);
-      const f2 fra = sub2(pa, fla), frb = sub2(pb, flb);
-      float x0a, x0b, y0a, y0b, fxa, fxb, fya, fyb;
-      unpack2(fla, x0a, y0a);
-      unpack2(flb, x0b, y0b);
-      unpack2(fra, fxa, fya);
-      unpack2(frb, fxb, fyb);
-      // texels: w (x0, y0), z (x0+1, y0), x (x0, y0+1), y (x0+1, y0+1)
-      const float4 ga = tex2Dgather<float4>(V.tex, x0a, y0a, 0);
-      const float4 gb = tex2Dgather<float4>(V.tex, x0b, y0b, 0);
-      const float ta = fmaf(fxa, ga.z - ga.w, ga.w), ba = fmaf(fxa, ga.y - ga.x, ga.x);
-      const float tb = fmaf(fxb, gb.z - gb.w, gb.w), bb = fmaf(fxb, gb.y - gb.x, gb.x);
-      const f2 sp = pack2(fmaf(fya, ba - ta, ta), fmaf(fyb, bb - tb, tb));
+      f2 sp;
+      if (kTex) {
+        // the texture unit's linear filter (AMH_FLAG_TEXTURE_BILINEAR): its
+        // texel centres sit at +0.5, the positions here at +1
+        const f2 ha = sub2(pa, pack2(0.5f, 0.5f)), hb = sub2(pb, pack2(0.5f, 0.5f));
+        float hxa, hya, hxb, hyb;
+        unpack2(ha, hxa, hya);
+        unpack2(hb, hxb, hyb);
+        sp = pack2(tex2D<float>(V.tex, hxa, hya), tex2D<float>(V.tex, hxb, hyb));
+      } else {
+        const f2 fla = floor2(pa), flb = floor2(pb);
+        const f2 fra = sub2(pa, fla), frb = sub2(pb, flb);
+        float x0a, x0b, y0a, y0b, fxa, fxb, fya, fyb;
+        unpack2(fla, x0a, y0a);
+        unpack2(flb, x0b, y0b);
+        unpack2(fra, fxa, fya);
+        unpack2(frb, fxb, fyb);
+        // texels: w (x0, y0), z (x0+1, y0), x (x0, y0+1), y (x0+1, y0+1)
+        const float4 ga = tex2Dgather<float4>(V.tex, x0a, y0a, 0);
+        const float4 gb = tex2Dgather<float4>(V.tex, x0b, y0b, 0);
+        const float ta = fmaf(fxa, ga.z - ga.w, ga.w), ba = fmaf(fxa, ga.y - ga.x, ga.x);
+        const float tb = fmaf(fxb, gb.z - gb.w, gb.w), bb = fmaf(fxb, gb.y - gb.x, gb.x);
+        sp = pack2(fmaf(fya, ba - ta, ta), fmaf(fyb, bb - tb, tb));
+      }
       // moments about the first sample: exact zero variance for constant
       // patches in FP32
       if (m == 0) {
@@ -360,6 +371,9 @@ __device__ __forceinline__ float kbest_mean(const float* m, int N, int k) {
 // refinement candidates) is scored by the mean of its own k smallest
 // per-view costs instead of MHJ, and no S_t / v_t is kept.
 constexpr int kSymmetric = 1, kHeuristic = 2;
+// kTexture: window samples through the texture unit's linear filter
+// (AMH_FLAG_TEXTURE_BILINEAR) instead of gathers and FP32 blends.
+constexpr int kTexture = 4;
 
 // ---------------------------------------------------------------------------
 // one pixel's checkerboard update
@@ -367,6 +381,7 @@ constexpr int kSymmetric = 1, kHeuristic = 2;
 template <bool kHalf, int kMode = 0, class A>
 __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x, int y,
                                              int* npairs) {
+  constexpr bool kTex = (kMode & kTexture) != 0;
   const int N = a.N;
   const size_t pi = (size_t)y * a.W + x;
   const float fx = (float)x, fy = (float)y;
@@ -429,7 +444,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     for (int g = 0; g < kRegions; g++) {
       const bool ok = valid >> g & 1u;
       const float3 c = ok ? make_float3(sm.cc(g, 0), sm.cc(g, 1), sm.cc(g, 2)) : make_float3(0.f, 0.f, 0.f);
-      sm.m(g, j, N) = ncc_cost<kHalf>(V, c, ok, fx, fy, rw, npairs);
+      sm.m(g, j, N) = ncc_cost<kHalf, kTex>(V, c, ok, fx, fy, rw, npairs);
     }
   }
 
@@ -438,7 +453,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     float4 best = a.plane[pi];
     float3 c;
     bool ok = plane_c(a.Kinv, best, ray, &c);
-    for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs);
+    for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs);
     float bm = kbest_mean(sm.w, N, k);
     int choice = 8;
     float bestD = 0.f;
@@ -460,7 +475,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 #pragma unroll 1
     for (int ci = 0; ci < nc; ci++) {
       ok = plane_c(a.Kinv, refine_candidate(a, x, y, best, ray, ci), ray, &c);
-      for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs);
+      for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs);
       const float m = kbest_mean(sm.w, N, k);
       if (bc < 0 || m < bcm) { bc = ci; bcm = m; }
     }
@@ -499,7 +514,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   float bm = 0.f;
   for (int j = 0; j < N; j++) {   // views with weight 0 are skipped (per-lane predicate)
     const float wj = sm.wt(j);
-    if (wj > 0.f) bm = fmaf(wj, ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs), bm);
+    if (wj > 0.f) bm = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs), bm);
   }
   bm *= inv_sw;
   int choice = 8;
@@ -552,7 +567,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     for (int j = 0; j < N; j++) {   // j stays warp-uniform (one texture per gather)
       const float wj = sm.wt(j);
       if (wj > 0.f && alive) {
-        m = fmaf(wj, ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs), m);
+        m = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs), m);
         alive = m * inv_sw < bound;
       }
     }
@@ -577,7 +592,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 // depth uniform in [d_min, d_max], normal uniform on the sphere flipped to
 // face the camera, draws (pixel, 0, 0, 0); the initial cost is the mean of the
 // k smallest per-view costs, summed in ascending order (ties: lower view).
-template <bool kHalf, class A>
+template <bool kHalf, bool kTex, class A>
 __device__ __forceinline__ void init_pixel(const A& a, PixelArrays& sm, int x, int y, int* npairs) {
   const int N = a.N;
   const size_t pi = (size_t)y * a.W + x;
@@ -590,7 +605,7 @@ __device__ __forceinline__ void init_pixel(const A& a, PixelArrays& sm, int x, i
   const bool ok = plane_c(a.Kinv, pl, ray, &c);
   RefWin rw;
   load_ref_window<kHalf>(a, x, y, rw);
-  for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf>(a.v[j], c, ok, fx, fy, rw, npairs);
+  for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs);
   // mean of the k smallest per-view costs, summed in ascending order (ties:
   // lower view index)
   const int k = a.k < N ? a.k : N;

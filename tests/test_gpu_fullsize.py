@@ -3,7 +3,8 @@ the launch configuration bench.py times: the GPU runs a whole colour phase;
 the FP64 oracle recomputes a sample of the updated pixels one by one from the
 same pre-phase state, and the two must keep the same plane with
 |dcost| <= 1e-4 on >= 99.9 % of the sampled pixels that are not near-ties.
-The same at full size with the images stored as FP16 (the precision form).
+The same at full size with the images stored as FP16, and with the samples
+interpolated by the texture unit's filter (the two precision forms).
 The error statistics are printed (run with -s to see them)."""
 import dataclasses
 
@@ -42,19 +43,20 @@ def _sample_pixels(W, H, color, n, rng):
     return np.concatenate([xs, bx[keep]]), np.concatenate([ys, by[keep]])
 
 
-@pytest.mark.parametrize("t,color,f16", [(1, 0, False), (4, 1, False), (2, 0, True)])
-def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color, f16):
+@pytest.mark.parametrize("t,color,form", [(1, 0, "u8"), (4, 1, "u8"), (2, 0, "f16"), (3, 1, "texture")])
+def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color, form):
     sc = large_scene
-    if f16:
+    if form == "f16":
         sc = dataclasses.replace(sc, images=[im.astype(np.float16) for im in sc.images])
+    flags = amh.AMH_FLAG_TEXTURE_BILINEAR if form == "texture" else 0
     W, H = sc.width, sc.height
-    g = amh.Context.from_scene(sc, seed=23)
+    g = amh.Context.from_scene(sc, seed=23, flags=flags)
     g.init_random()
     g.iterate(2)
     pre = g.get_state()
     # the same FP32 state in both, iteration index t
     g.set_state(pre["plane"], pre["cost"], pre["sel"], pre["vbest"], pre["wmask"], pre["choice"], t=t)
-    o = oracle_mod.Oracle.from_scene(sc, seed=23)
+    o = oracle_mod.Oracle.from_scene(sc, seed=23, flags=flags)
     vb = pre["vbest"].astype(np.int32)
     vprev = np.where(vb == 255, -1, vb).astype(np.int32)
     o.set_state(plane=pre["plane"].astype(np.float64), cost=pre["cost"].astype(np.float64), sel=pre["sel"],
@@ -79,7 +81,7 @@ def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color, f16):
     n = len(xs)
     frac = n_ok / max(1, n - n_tie)
     dc = np.array(dc)
-    print(f"\nfull size t={t} colour={color} {'FP16' if f16 else 'uint8'} images: {n} pixels, same plane and |dcost|<=1e-4 on {n_ok}, "
+    print(f"\nfull size t={t} colour={color} {form} form: {n} pixels, same plane and |dcost|<=1e-4 on {n_ok}, "
           f"near-ties {n_tie}; |dcost| on same plane: median {np.median(dc):.2e}, "
           f"99.9% {np.quantile(dc, 0.999):.2e}, max {dc.max():.2e}")
     assert frac >= FRACTION, (n_ok, n_tie, n)

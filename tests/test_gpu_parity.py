@@ -221,6 +221,66 @@ def test_phase_parity_flags(oracle_mod, amh, tiny_scene, flags, t):
         assert (g.get_state()["vbest"] == 255).all()
 
 
+@pytest.mark.parametrize("t", [0, 1, 4])
+def test_texture_bilinear_parity(oracle_mod, amh, tiny_scene, t):
+    """The texture-filter precision form against the oracle's texture-unit
+    sampling (fractions and their product rounded to 1/256): initial costs,
+    then one phase of each colour from identical state."""
+    f = amh.AMH_FLAG_TEXTURE_BILINEAR
+    o, g = _pair(oracle_mod, amh, tiny_scene, seed=70 + t, flags=f)
+    if t == 0:
+        o.init_random()
+        g.init_random()
+        g.synchronize()
+        d = np.abs(o.get_state()["cost"] - g.get_state()["cost"])
+        assert (d <= COST_TOL).mean() >= FRACTION, np.sort(d.ravel())[-10:]
+    o.init_random()
+    o.iterate(min(t, 2))
+    st = o.get_state()
+    st["t"] = t
+    for color in (0, 1):
+        r = phase_check(o, g, st, color)
+        assert r["frac_ok_nontie"] >= FRACTION, r
+        assert r["frac_sel"] >= FRACTION and r["frac_v"] >= FRACTION, r
+
+
+def test_texture_bilinear_whole_run(oracle_mod, amh, tiny_scene):
+    """Init + 3 iterations in the texture form on both sides: final depth
+    within 1 % relative on >= 99 % of valid pixels, and as close to the
+    ground truth as the default form."""
+    sc = tiny_scene
+    f = amh.AMH_FLAG_TEXTURE_BILINEAR
+    o, g = _pair(oracle_mod, amh, sc, seed=7, flags=f)
+    o.init_random()
+    o.iterate(3)
+    g.init_random()
+    g.iterate(3)
+    Do = o.depth_map()
+    Dg = g.read_maps()["depth"].astype(np.float64)
+    m = valid_pixels(sc)
+    rel = np.abs(Dg - Do) / Do
+    assert (rel[m] <= 0.01).mean() >= 0.99, (rel[m] <= 0.01).mean()
+    d = amh.Context.from_scene(sc, seed=7)
+    d.init_random()
+    d.iterate(3)
+    gt = sc.gt_depth[sc.ref].astype(np.float64)
+    acc = lambda D: float((np.abs(D - gt)[m] <= 0.01 * gt[m]).mean())
+    assert acc(Dg) >= acc(d.read_maps()["depth"].astype(np.float64)) - 0.01
+
+
+def test_texture_bilinear_rejected_combinations(amh, tiny_scene):
+    sc = tiny_scene
+    t = amh.AMH_FLAG_TEXTURE_BILINEAR
+    for extra in (amh.AMH_FLAG_IMAGES_F16, amh.AMH_FLAG_SYMMETRIC_PROPAGATION, amh.AMH_FLAG_HEURISTIC_VIEWS):
+        imgs = [im.astype(np.float16) for im in sc.images] if extra == amh.AMH_FLAG_IMAGES_F16 else sc.images
+        p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=t | extra)
+        with pytest.raises(amh.AmhError):
+            amh.Context(sc.cams, imgs, sc.ref, sc.src, p)
+    p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=t)
+    with pytest.raises(amh.AmhError):
+        amh.Batch(sc.cams, sc.images, [sc.ref], [sc.src], p)
+
+
 def test_ablations_rejected_by_the_batch(amh, tiny_scene):
     sc = tiny_scene
     p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=amh.AMH_FLAG_HEURISTIC_VIEWS)
