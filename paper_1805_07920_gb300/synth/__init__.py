@@ -18,6 +18,8 @@ Named workloads (sizes and structure of the paper's multi-view workloads):
              views as sources; 8 x 1920x1080, 6 x 2560x1440, 6 x 3200x2112.
 ``learned``  1600x1056, 1 + 10, multi-object scene whose layout depends on the
              seed (training and held-out scenes).
+``fusion``   160x120, 5 cameras with ground truth in every view (fusion tests).
+``many``     96x72, 1 + 32 cameras on a 60 degree arc (the largest source count).
 """
 from __future__ import annotations
 
@@ -214,6 +216,24 @@ def scene_fusion(seed=6, n=5):
     return Scene("fusion", seed, cams, imgs, ref, src, 2.0, 8.0, gd, gn)
 
 
+def scene_many(seed=7, n=33, width=96, height=72):
+    """The tiny scene's two slanted planes seen by n cameras on a 60-degree
+    arc at 96x72: the middle one is the reference, the other n - 1 its
+    sources (n = 33 gives the largest source count, 32)."""
+    f = 0.9 * width
+    cams = _arc_cams(n, width, height, f, radius=4.0, arc_deg=60.0)
+    tf = _tex_freq(4.0, f)
+    prims = [
+        _prim(SYN_QUAD, a=(-0.9, 0, -0.3), b=(1.2 * math.cos(0.52), 0, 1.2 * math.sin(0.52)),
+              c=(0, 2.5, 0), albedo=0.5, tex_freq=tf, tex_off=3.1),
+        _prim(SYN_PLANE, a=(0, math.sin(0.44), -math.cos(0.44)), b=(1.2, 0, 0), albedo=0.5,
+              tex_freq=tf, tex_off=11.7),
+    ]
+    ref, src = _centre_first(n)
+    imgs, gd, gn = render(cams, prims, seed, gt_views=(ref,))
+    return Scene("many", seed, cams, imgs, ref, src, 2.0, 8.0, gd, gn)
+
+
 def scene_medium(seed=2):
     W, H, f = 640, 480, 560.0
     cams = _arc_cams(6, W, H, f, radius=6.0, arc_deg=40.0, height_off=-0.8)
@@ -323,7 +343,7 @@ def ring_sources(ref, n=20, n_src=10):
 
 
 SCENES = {"tiny": scene_tiny, "medium": scene_medium, "large": scene_large,
-          "ring20": scene_ring20, "learned": scene_learned, "fusion": scene_fusion}
+          "ring20": scene_ring20, "learned": scene_learned, "fusion": scene_fusion, "many": scene_many}
 
 
 def make_scene(name: str, seed: int | None = None, cache_dir: str | None = None) -> Scene:

@@ -281,6 +281,32 @@ def test_texture_bilinear_rejected_combinations(amh, tiny_scene):
         amh.Batch(sc.cams, sc.images, [sc.ref], [sc.src], p)
 
 
+@pytest.mark.parametrize("n_src", [1, 32])
+@pytest.mark.parametrize("t", [1, 4])
+def test_source_count_bounds(oracle_mod, amh, synth_mod, n_src, t):
+    """The fewest and the most source views (1: k is clamped to N and the
+    good/bad counts of MHJ run over one column; 32: every bit of the view
+    masks in use): initial costs and one phase of each colour."""
+    import dataclasses
+    sc = synth_mod.make_scene("many")
+    sc = dataclasses.replace(sc, src=list(sc.src[:n_src]))
+    o, g = _pair(oracle_mod, amh, sc, seed=80 + t)
+    o.init_random()
+    g.init_random()
+    g.synchronize()
+    d = np.abs(o.get_state()["cost"] - g.get_state()["cost"])
+    assert (d <= COST_TOL).mean() >= FRACTION, np.sort(d.ravel())[-10:]
+    o.iterate(min(t, 2))
+    st = o.get_state()
+    st["t"] = t
+    for color in (0, 1):
+        r = phase_check(o, g, st, color)
+        assert r["frac_ok_nontie"] >= FRACTION, r
+        assert r["frac_sel"] >= FRACTION and r["frac_v"] >= FRACTION, r
+    if n_src == 32:
+        assert (g.get_state()["wmask"] >> 31 & 1).any()     # the 32nd view does get weight
+
+
 def test_ablations_rejected_by_the_batch(amh, tiny_scene):
     sc = tiny_scene
     p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=amh.AMH_FLAG_HEURISTIC_VIEWS)
