@@ -463,7 +463,23 @@ def bench_batch(args, dist):
     px = sum(w * h for (w, h, _) in b.sizes)
     post = postprocess(b, sc, refs)
     b.close()
+    # the same batch in the texture-filter precision form, same tile variant
+    pt = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=SEED,
+                            flags=amh.AMH_FLAG_TEXTURE_BILINEAR)
+    bt = amh.Batch(sc.cams, sc.images, refs, srcs, pt)
+    bt.set_variant(chosen)
+    bt.run(ITERS)
+    bt.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        bt.run(ITERS)
+    bt.synchronize()
+    ms_t = (time.perf_counter() - t0) * 1e3
+    bt.close()
+    texture = {"value": round(px * ITERS * steps / (ms_t / 1e3) / 1e6, 3), "ms_per_batch": round(ms_t / steps, 3),
+               "flags": "AMH_FLAG_TEXTURE_BILINEAR"}
     return {"metric": "Mpixel-iterations/s over all 20 references", "unit": UNIT, "postprocess": post,
+            "texture_bilinear": texture,
             "value": round(px * ITERS * steps / (ms / 1e3) / 1e6, 3), "ms_per_batch": round(ms / steps, 3),
             "pixels_per_iteration": px, "pairs_per_batch": pairs, "launches_per_batch": 1 + 2 * ITERS,
             "tile_variant": ["16x16", "32x8", "64x4"][chosen],

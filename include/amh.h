@@ -81,8 +81,8 @@ enum {
    * the interpolation): the texture unit's linear filter interpolates, with
    * its fractions and their product rounded half up to 1/256, instead of
    * FP32 blends of gathered texels (fewer instructions per sample).  uint8
-   * images and the method's own propagation / view selection only; single
-   * contexts only (amh_create / amh_batch_create reject other combinations). */
+   * images and the method's own propagation / view selection only (amh_create
+   * and amh_batch_create reject other combinations). */
   AMH_FLAG_TEXTURE_BILINEAR = 16
 };
 

@@ -4,8 +4,8 @@
                              (nvcc, sm_103a only, static cudart, no torch types).
 * ``_lib/libscenegen.so`` -- the seeded synthetic-scene ray caster (gcc, OpenMP).
 
-Both compile in parallel in a few seconds; nothing is installed outside the
-source tree.
+The CUDA sources compile one object each, side by side, then link; nothing
+is installed outside the source tree.
 """
 from __future__ import annotations
 
@@ -18,6 +18,7 @@ import sys
 PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 REPO_DIR = os.path.dirname(PKG_DIR)
 LIB_DIR = os.path.join(PKG_DIR, "_lib")
+OBJ_DIR = os.path.join(LIB_DIR, "obj")
 CSRC = os.path.join(PKG_DIR, "csrc")
 INCLUDE = os.path.join(REPO_DIR, "include")
 
@@ -35,42 +36,44 @@ def amh_sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def commands(extra_nvcc: list[str] | None = None) -> list[tuple[str, list[str]]]:
-    os.makedirs(LIB_DIR, exist_ok=True)
-    cmds = []
-    srcs = amh_sources()
-    if srcs:
-        out = os.path.join(LIB_DIR, "libamh.so")
-        cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-               "-I", INCLUDE, "-o", out, *srcs]
-        if extra_nvcc:
-            cmd[1:1] = extra_nvcc
-        cmds.append((out, cmd))
-    sg = os.path.join(PKG_DIR, "synth", "scenegen.c")
-    out = os.path.join(LIB_DIR, "libscenegen.so")
-    cmds.append((out, ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                       "-o", out, sg, "-lm"]))
-    return cmds
+def _run_all(cmds: list[list[str]], verbose: bool) -> None:
+    """Run the commands side by side; raise with the log of the first failure."""
+    procs = []
+    for cmd in cmds:
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    failed = None
+    for cmd, p in procs:
+        log, _ = p.communicate()
+        if p.returncode != 0 and failed is None:
+            failed = f"build failed ({' '.join(cmd)}):\n{log}"
+        elif verbose and log.strip():
+            print(log, file=sys.stderr)
+    if failed:
+        raise RuntimeError(failed)
 
 
 def build(verbose: bool = False, extra_nvcc: list[str] | None = None) -> list[str]:
-    """Compile every native library of the package; raise on any failure."""
-    procs = []
-    for out, cmd in commands(extra_nvcc):
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((out, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
-                                                 stderr=subprocess.STDOUT, text=True)))
-    outs = []
-    for out, cmd, p in procs:
-        log, _ = p.communicate()
-        if p.returncode != 0:
-            raise RuntimeError(f"build failed ({' '.join(cmd)}):\n{log}")
-        if verbose and log.strip():
-            print(log, file=sys.stderr)
-        outs.append(out)
-    return outs
+    """Compile every native library of the package; raise on any failure.
+    Each CUDA source compiles to its own object at the same time as the
+    others (and the scene generator), then one link makes ``libamh.so``."""
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    nvcc = _nvcc()
+    flags = [*(extra_nvcc or []), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+             "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE]
+    objs, cmds = [], []
+    for src in amh_sources():
+        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        objs.append(obj)
+        cmds.append([nvcc, *flags, "-c", "-o", obj, src])
+    sg = os.path.join(PKG_DIR, "synth", "scenegen.c")
+    scenegen = os.path.join(LIB_DIR, "libscenegen.so")
+    cmds.append(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", scenegen, sg, "-lm"])
+    _run_all(cmds, verbose)
+    lib = os.path.join(LIB_DIR, "libamh.so")
+    _run_all([[nvcc, *ARCH, "-shared", "-o", lib, *objs]], verbose)
+    return [lib, scenegen]
 
 
 if __name__ == "__main__":

@@ -69,7 +69,7 @@ struct TileShape {
   static constexpr int cols = TW / 2, rows = kBThreads / cols;
 };
 
-template <bool kHalf, int TW>
+template <bool kHalf, int TW, int kMode>
 __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ RefArgs ra;
   __shared__ int cur_ref;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_
     const int x = tx * TW + 2 * (threadIdx.x % T::cols) + ((y + b.color) & 1);
     if (x < ra.W && y < ra.H) {
       PixelArrays sm;
-      update_pixel<kHalf>(ra, sm, x, y, &npairs);
+      update_pixel<kHalf, kMode>(ra, sm, x, y, &npairs);
     }
   }
   const int tot = __reduce_add_sync(0xffffffffu, npairs);
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_
 }
 
 // random initialisation of every pixel of every reference: 16 x 8 pixel tiles
-template <bool kHalf>
+template <bool kHalf, bool kTex>
 __global__ void __launch_bounds__(kBThreads) batch_init_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ RefArgs ra;
   __shared__ int cur_ref;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBThreads) batch_init_kernel(const __grid_cons
     const int x = tx * 16 + (threadIdx.x & 15), y = ty * 8 + (threadIdx.x >> 4);
     if (x < ra.W && y < ra.H) {
       PixelArrays sm;
-      init_pixel<kHalf, false>(ra, sm, x, y, &npairs);
+      init_pixel<kHalf, kTex>(ra, sm, x, y, &npairs);
     }
   }
   const int tot = __reduce_add_sync(0xffffffffu, npairs);
@@ -155,6 +155,7 @@ struct amh_batch {
   amh_params p;
   int n_views = 0, n_refs = 0;
   bool half = false;
+  bool tex_filter = false;   // AMH_FLAG_TEXTURE_BILINEAR
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<cudaArray_t> arr;
@@ -263,18 +264,21 @@ BatchArgs make_args(amh_batch* b, const RefArgs* refs, int n_items, int color) {
   return a;
 }
 
-template <bool kHalf>
+template <bool kHalf, int kMode>
 void launch_batch_phase(amh_batch* b, int color) {
   const BatchArgs a = make_args(b, b->d_refs[b->variant], b->items[b->variant], color);
   switch (kTileW[b->variant]) {
-    case 16: batch_phase_kernel<kHalf, 16><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
-    case 32: batch_phase_kernel<kHalf, 32><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
-    default: batch_phase_kernel<kHalf, 64><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
+    case 16: batch_phase_kernel<kHalf, 16, kMode><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
+    case 32: batch_phase_kernel<kHalf, 32, kMode><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
+    default: batch_phase_kernel<kHalf, 64, kMode><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
   }
 }
+// FP16 images, uint8 images, or uint8 images through the texture unit's
+// linear filter (AMH_FLAG_TEXTURE_BILINEAR; not combined with FP16)
 int batch_phase(amh_batch* b, int color) {
-  if (b->half) launch_batch_phase<true>(b, color);
-  else launch_batch_phase<false>(b, color);
+  if (b->tex_filter) launch_batch_phase<false, kTexture>(b, color);
+  else if (b->half) launch_batch_phase<true, 0>(b, color);
+  else launch_batch_phase<false, 0>(b, color);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(b, AMH_ECUDA, "batch phase launch: %s", cudaGetErrorString(e));
   if (color == 1) b->t++;
@@ -283,8 +287,9 @@ int batch_phase(amh_batch* b, int color) {
 int batch_init(amh_batch* b) {
   b->t = 0;
   const BatchArgs a = make_args(b, b->d_refs_init, b->init_items, 0);
-  if (b->half) batch_init_kernel<true><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
-  else batch_init_kernel<false><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
+  if (b->tex_filter) batch_init_kernel<false, true><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
+  else if (b->half) batch_init_kernel<true, false><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
+  else batch_init_kernel<false, false><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(b, AMH_ECUDA, "batch init launch: %s", cudaGetErrorString(e));
   b->initialized = true;
@@ -308,8 +313,10 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
   if (!(p->k >= 1) || p->n1 < 0 || p->n2 < 0 || !(p->beta > 0) || !(p->sigma_I > 0) || !(p->sigma_x > 0) ||
       !(p->alpha > 0) || !(p->depth_min > 0) || !(p->depth_max > p->depth_min))
     return bfail(nullptr, AMH_EINVAL, "invalid parameters");
-  if (p->flags & (AMH_FLAG_SYMMETRIC_PROPAGATION | AMH_FLAG_HEURISTIC_VIEWS | AMH_FLAG_TEXTURE_BILINEAR))
-    return bfail(nullptr, AMH_EINVAL, "the ablation and texture-filter flags apply to single contexts only");
+  if (p->flags & (AMH_FLAG_SYMMETRIC_PROPAGATION | AMH_FLAG_HEURISTIC_VIEWS))
+    return bfail(nullptr, AMH_EINVAL, "the ablation flags apply to single contexts only");
+  if ((p->flags & AMH_FLAG_TEXTURE_BILINEAR) && (p->flags & AMH_FLAG_IMAGES_F16))
+    return bfail(nullptr, AMH_EINVAL, "AMH_FLAG_TEXTURE_BILINEAR takes uint8 images");
   if (src_offsets[0] != 0) return bfail(nullptr, AMH_EINVAL, "src_offsets[0] must be 0");
   for (int r = 0; r < n_refs; r++) {
     const int ref = refs[r];
@@ -349,6 +356,7 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
   b->n_views = n_views;
   b->n_refs = n_refs;
   b->half = (p->flags & AMH_FLAG_IMAGES_F16) != 0;
+  b->tex_filter = (p->flags & AMH_FLAG_TEXTURE_BILINEAR) != 0;
   if (stream) b->stream = (cudaStream_t)stream;
   else {  // graph capture needs a stream other than the legacy default stream
     CB(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
@@ -381,7 +389,7 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
     cudaTextureDesc td;
     std::memset(&td, 0, sizeof td);
     td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
-    td.filterMode = cudaFilterModePoint;
+    td.filterMode = b->tex_filter ? cudaFilterModeLinear : cudaFilterModePoint;
     td.readMode = b->half ? cudaReadModeElementType : cudaReadModeNormalizedFloat;
     CB(cudaCreateTextureObject(&b->tex[v], &rd, &td, nullptr));
   }

@@ -34,8 +34,8 @@ def _lists(ring, synth_mod, n=6, n_src=3):
     return refs, [synth_mod.ring_sources(r, n, n_src) for r in refs]
 
 
-def _single(amh, ring, r, src, seed, iters):
-    p = amh.default_params(depth_min=ring.depth_min, depth_max=ring.depth_max, seed=seed + r)
+def _single(amh, ring, r, src, seed, iters, flags=0):
+    p = amh.default_params(depth_min=ring.depth_min, depth_max=ring.depth_max, seed=seed + r, flags=flags)
     g = amh.Context(ring.cams, ring.images, r, src, p)
     g.init_random()
     g.iterate(iters)
@@ -52,6 +52,23 @@ def test_batch_equals_single_contexts(amh, ring, synth_mod):
         s1 = _single(amh, ring, r, srcs[r], 70, 2)
         sb = b.get_state(r)
         assert sb["t"] == 2
+        for k in KEYS:
+            np.testing.assert_array_equal(sb[k], s1[k], err_msg=f"ref {r} {k}")
+
+
+def test_batch_texture_form_equals_single_contexts(amh, ring, synth_mod):
+    """The texture-filter precision form batched: bit for bit the single
+    contexts of that form (those are parity-checked against the oracle's
+    texture-unit sampling)."""
+    refs, srcs = _lists(ring, synth_mod)
+    f = amh.AMH_FLAG_TEXTURE_BILINEAR
+    p = amh.default_params(depth_min=ring.depth_min, depth_max=ring.depth_max, seed=75, flags=f)
+    b = amh.Batch(ring.cams, ring.images, refs, srcs, p)
+    b.init_random()
+    b.iterate(4)
+    for r in refs:
+        s1 = _single(amh, ring, r, srcs[r], 75, 4, flags=f)
+        sb = b.get_state(r)
         for k in KEYS:
             np.testing.assert_array_equal(sb[k], s1[k], err_msg=f"ref {r} {k}")
 

@@ -276,9 +276,9 @@ def test_texture_bilinear_rejected_combinations(amh, tiny_scene):
         p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=t | extra)
         with pytest.raises(amh.AmhError):
             amh.Context(sc.cams, imgs, sc.ref, sc.src, p)
-    p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=t)
+    p = amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, flags=t | amh.AMH_FLAG_IMAGES_F16)
     with pytest.raises(amh.AmhError):
-        amh.Batch(sc.cams, sc.images, [sc.ref], [sc.src], p)
+        amh.Batch(sc.cams, [im.astype(np.float16) for im in sc.images], [sc.ref], [sc.src], p)
 
 
 @pytest.mark.parametrize("n_src", [1, 32])
