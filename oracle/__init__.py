@@ -23,7 +23,7 @@ ORC_FLAG_TEXTURE_BILINEAR = 16  # bilinear weights as a texture unit's linear fi
 
 
 def build_command() -> list[str]:
-    return ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", LIB_PATH,
+    return ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", LIB_PATH,
             os.path.join(ORACLE_DIR, "amh_oracle.c"), "-lm"]
 
 
@@ -67,6 +67,7 @@ def lib():
                                  ctypes.POINTER(_dp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.c_int]
         L.orc_destroy.argtypes = [_vp]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_width.argtypes = [_vp]
         L.orc_height.argtypes = [_vp]
         L.orc_set_state.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
@@ -141,6 +142,12 @@ def tau_mc(t: int, params: OrcParams | None = None) -> float:
 def confidence(m: float, params: OrcParams | None = None) -> float:
     p = params or default_params()
     return lib().orc_confidence(ctypes.byref(p), m)
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's pixel loops (default 1; timing only -- the
+    results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def bilinear(img: np.ndarray, x: float, y: float) -> float:

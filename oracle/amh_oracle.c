@@ -719,9 +719,17 @@ void orc_update_pixels(orc_ctx* c, int n, const int32_t* xs, const int32_t* ys) 
   }
 }
 
+/* Threads for the pixel loops (1 unless orc_set_threads asks for more; used
+ * only to time the oracle on all host cores -- the pixels of one colour
+ * phase, and of the initialisation, are independent, so the results do not
+ * depend on it). */
+static int g_threads = 1;
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
 /* red/black checkerboard (Sec. 3.1, Fig. 2(a)): a pixel of one colour reads
  * only pixels of the other colour, so the order inside a phase is free */
 void orc_step_phase(orc_ctx* c, int color) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
   for (int y = 0; y < c->H; y++)
     for (int x = 0; x < c->W; x++) {
       if (((x + y) & 1) != color) continue;
@@ -741,6 +749,7 @@ void orc_iterate(orc_ctx* c, int k) {
 void orc_init_random(orc_ctx* c) {
   const int N = c->n_src;
   int k = c->p.k < N ? c->p.k : N;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
   for (int y = 0; y < c->H; y++)
     for (int x = 0; x < c->W; x++) {
       size_t pi = (size_t)y * c->W + x;

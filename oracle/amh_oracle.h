@@ -88,6 +88,9 @@ void orc_get_state(const orc_ctx* c, double* plane, double* cost, uint32_t* sel,
 void orc_init_random(orc_ctx* c);
 /* One colour phase at the current t (color 0 = black: (x+y) even).  After
  * the red phase (color 1) t advances by one. */
+/* threads of the pixel loops of orc_step_phase / orc_init_random (default
+ * 1; the results do not depend on it) */
+void orc_set_threads(int n);
 void orc_step_phase(orc_ctx* c, int color);
 void orc_iterate(orc_ctx* c, int k);
 /* One pixel's update from the current state, without writing it. */
