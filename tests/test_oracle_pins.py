@@ -691,3 +691,21 @@ def test_heuristic_view_selection(oracle_mod, tiny_scene, flags):
             if row is not None:
                 assert u["cost"] <= kb(row) + 1e-15
         assert o.score_plane(x, y, u["plane"]) == pytest.approx(u["cost"], rel=1e-12, abs=1e-15)
+
+
+def test_threaded_oracle_gives_identical_results(oracle_mod, tiny_scene):
+    """The thread count of the oracle's pixel loops (used only to time it on
+    all host cores) does not change any result: the pixels of one colour phase
+    read only the other colour."""
+    out = []
+    try:
+        for th in (1, 4):
+            oracle_mod.set_threads(th)
+            o = oracle_mod.Oracle.from_scene(tiny_scene, seed=12)
+            o.init_random()
+            o.iterate(1)
+            out.append(o.get_state())
+    finally:
+        oracle_mod.set_threads(1)
+    for k in ("plane", "cost", "sel", "vprev", "choice"):
+        np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
