@@ -53,9 +53,9 @@ FLOP_PER_PAIR = SAMPLES_PER_PAIR * FLOP_PER_SAMPLE + FLOP_PER_PAIR_SETUP
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum per phase launch from an ncu
 # capture, keyed by the hash of the phase kernel's sources it was taken on
-# (null whenever they changed since).
+# and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "64cce607fc40caf5": 271246080.0 + 239685888.0,   # profiles/phase_kernel_large.md
+    "64cce607fc40caf5/fp32_blend": 271246080.0 + 239685888.0,   # profiles/phase_kernel_large.md
 }
 
 
@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-form and learned-proposal measurements (run only at N = 1)")
+    ap.add_argument("--texture-bilinear", action="store_true",
+                    help="time the texture-filter precision form (AMH_FLAG_TEXTURE_BILINEAR) instead of the "
+                         "default FP32-blend form")
     return ap.parse_args()
 
 
@@ -250,7 +253,9 @@ def run_ours(args):
     amh.lib()
     sc = rank_scene(rank)
     W, H = sc.width, sc.height
-    ctx = amh.Context.from_scene(sc, seed=SEED)
+    form_flags = amh.AMH_FLAG_TEXTURE_BILINEAR if args.texture_bilinear else 0
+    form = "texture_bilinear" if args.texture_bilinear else "fp32_blend"
+    ctx = amh.Context.from_scene(sc, seed=SEED, flags=form_flags)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -306,7 +311,7 @@ def run_ours(args):
     achieved = flop_per_launch / (phase_ms / 1e3) / 1e12
     khash = kernel_source_hash()
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": KNOWN_TRAFFIC.get(khash),
+                "frac": round(achieved / peak, 4), "traffic": KNOWN_TRAFFIC.get(f"{khash}/{form}"),
                 "kernel": "phase_kernel", "launch_ms": round(phase_ms, 3),
                 "flop_per_launch": flop_per_launch, "pairs_per_launch": pairs_phase / (2 * ITERS),
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
@@ -333,7 +338,8 @@ def run_ours(args):
 
         def e2e_step():
             c = amh.Context(sc.cams, host_imgs, sc.ref, sc.src,
-                            amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=SEED))
+                            amh.default_params(depth_min=sc.depth_min, depth_max=sc.depth_max, seed=SEED,
+                                               flags=form_flags))
             c.init_random()
             c.iterate(ITERS)
             amh.lib().amh_read_maps(c.ctx, amh._ptr(outs["depth"].numpy()), amh._ptr(outs["normal"].numpy()),
@@ -357,7 +363,8 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and world == 1:     # one-GPU measurements of the other forms
-        extras["texture_bilinear_3200x2112"] = bench_texture(sc, args.steps, phase_ms, ctx)
+        if not args.texture_bilinear:
+            extras["texture_bilinear_3200x2112"] = bench_texture(sc, args.steps, phase_ms, ctx)
         extras["batched_ring20"] = bench_batch(args, dist)
         extras["learned_proposal_1600x1056"] = bench_learned()
 
@@ -380,7 +387,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ray-cast scene)",
-            "config": workload_config(sc) | {"parallelism": f"replicas{world}: one reference view per GPU"},
+            "config": workload_config(sc) | {"parallelism": f"replicas{world}: one reference view per GPU",
+                                             "interpolation": form},
             "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "extras": extras,
             "clocks": clocks, "gpu_launches": args.steps * (1 + 2 * ITERS),
