@@ -55,7 +55,8 @@ FP32_LANES_PER_SM = 128
 # capture, keyed by the hash of the phase kernel's sources it was taken on
 # and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "64cce607fc40caf5/fp32_blend": 271246080.0 + 239685888.0,   # profiles/phase_kernel_large.md
+    "c977d86fb4522a9c/fp32_blend": 272470528.0 + 240014336.0,         # profiles/phase_kernel_large.md
+    "c977d86fb4522a9c/texture_bilinear": 270164736.0 + 236200704.0,   # profiles/phase_kernel_texture_large.md
 }
 
 
