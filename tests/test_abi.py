@@ -84,7 +84,8 @@ def _create(cams, images, ref, src, params=None, mem=0):
 
 
 @pytest.mark.parametrize("case", ["n_src0", "n_src33", "src_is_ref", "src_repeat", "bad_ref", "bad_window",
-                                  "bad_K", "null_image", "bad_mem", "bad_depth_range"])
+                                  "bad_K", "null_image", "bad_mem", "bad_depth_range", "empty_image",
+                                  "texture_f16", "texture_ablation"])
 def test_invalid_arguments_rejected_on_host(built, case):
     from paper_1805_07920_gb300 import amh
     cams = _cams()
@@ -112,6 +113,12 @@ def test_invalid_arguments_rejected_on_host(built, case):
         mem = 7
     elif case == "bad_depth_range":
         p.depth_min, p.depth_max = 5.0, 1.0
+    elif case == "empty_image":
+        cams[2].width = 0
+    elif case == "texture_f16":
+        p.flags = amh.AMH_FLAG_TEXTURE_BILINEAR | amh.AMH_FLAG_IMAGES_F16
+    elif case == "texture_ablation":
+        p.flags = amh.AMH_FLAG_TEXTURE_BILINEAR | amh.AMH_FLAG_SYMMETRIC_PROPAGATION
     rc, msg, ctx = _create(cams, imgs, ref, src, p, mem)
     assert rc == amh.AMH_EINVAL, (rc, msg)
     assert msg and not ctx.value
