@@ -3,6 +3,8 @@
 // update itself is in amh_update.cuh).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "amh_device.cuh"
 #include "amh_kernels.h"
 #include "amh_update.cuh"
@@ -47,15 +49,21 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
 }  // namespace
 
 // Both kernels use no shared memory: ask for the largest L1 (texture cache).
+// The preference is per device, so it is set once for each device that
+// launches the kernel.
 template <typename K>
-void prefer_l1(K kernel) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+void prefer_l1(K kernel, std::once_flag* once) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(once[dev & 63], [kernel] {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  });
 }
 
 template <bool kHalf, bool kTex>
 int launch_init_t(const PhaseArgs& a, cudaStream_t s) {
-  static bool once = (prefer_l1(init_kernel<kHalf, kTex>), true);
-  (void)once;
+  static std::once_flag once[64];
+  prefer_l1(init_kernel<kHalf, kTex>, once);
   dim3 grid((a.W + kTile - 1) / kTile, (a.H + 7) / 8);
   init_kernel<kHalf, kTex><<<grid, kThreads, 0, s>>>(a);
   return (int)cudaGetLastError();
@@ -69,8 +77,8 @@ int launch_init(const PhaseArgs& a, cudaStream_t s) {
 
 template <bool kHalf, int kMode>
 int launch_phase_t(const PhaseArgs& a, cudaStream_t s) {
-  static bool once = (prefer_l1(phase_kernel<kHalf, kMode>), true);
-  (void)once;
+  static std::once_flag once[64];
+  prefer_l1(phase_kernel<kHalf, kMode>, once);
   dim3 grid((a.W + kTile - 1) / kTile, (a.H + kTile - 1) / kTile);
   phase_kernel<kHalf, kMode><<<grid, kThreads, 0, s>>>(a);
   return (int)cudaGetLastError();
