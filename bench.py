@@ -55,8 +55,8 @@ FP32_LANES_PER_SM = 128
 # capture, keyed by the hash of the phase kernel's sources it was taken on
 # and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "c977d86fb4522a9c/fp32_blend": 272470528.0 + 240014336.0,         # profiles/phase_kernel_large.md
-    "c977d86fb4522a9c/texture_bilinear": 270164736.0 + 236200704.0,   # profiles/phase_kernel_texture_large.md
+    "2d03935d032f1a2a/fp32_blend": 270454016.0 + 238643712.0,         # profiles/phase_kernel_large.md
+    "2d03935d032f1a2a/texture_bilinear": 271075328.0 + 235463936.0,   # profiles/phase_kernel_texture_large.md
 }
 
 
