@@ -293,6 +293,23 @@ AMH_API int amh_net_adam(amh_net* net, float lr);
 AMH_API int amh_net_propose(amh_net* net, amh_ctx* ctx);
 /* Stop scoring proposals in the context. */
 AMH_API int amh_clear_proposal(amh_ctx* ctx);
+/* Proposals from any source (another network, a prior reconstruction): one
+ * plane per cell of a width2 x height2 grid, cell (X, Y) serving the pixels
+ * (2X .. 2X+1, 2Y .. 2Y+1) (cells past the grid's edge repeat its last row /
+ * column; width2 = ceil(W/2), height2 = ceil(H/2) covers the image).  Layout
+ * height2 x width2 x 4 floats (nx, ny, nz, d): the plane n . X + d = 0 in
+ * reference-camera coordinates, n facing the camera.  At each pixel it is
+ * scored like amh_net_propose's planes (one more refinement candidate under
+ * the pixel's view weights, winning choice code 15; not under the
+ * AMH_FLAG_HEURISTIC_VIEWS ablation, which has no view weights); a cell with d <= 0, or
+ * whose plane does not meet the pixel's ray in front of the camera, proposes
+ * nothing.  The planes are copied (mem: AMH_MEM_HOST or AMH_MEM_DEVICE) on
+ * the context's stream into a buffer the context owns; they stay in use
+ * until amh_clear_proposal, another amh_set_proposal or amh_net_propose.
+ * Errors: AMH_EINVAL for a NULL context / buffer, an empty grid or a bad mem;
+ * AMH_ENOMEM / AMH_ECUDA from the runtime. */
+AMH_API int amh_set_proposal(amh_ctx* ctx, const float* plane4, int32_t width2, int32_t height2,
+                             int32_t mem);
 /* Internal tensors, for element-wise checks of every operation: which =
  * 0..17 the forward tensors x0 e1 in_e2 e2 in_e3 e3 in_e4 e4 in_d3 r3 d3
  * in_d2 r2 d2 in_d1 r1 d1 out (in_* = pooled / upsampled inputs, r* = a

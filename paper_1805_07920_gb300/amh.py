@@ -34,7 +34,7 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
            "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
            "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
-           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse", "amh_select_sources"]
+           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse", "amh_select_sources", "amh_set_proposal"]
 
 
 class AmhError(RuntimeError):
@@ -621,6 +621,24 @@ class Net:
     def load(self, path):
         z = np.load(path)
         self.set_params({name: (z[f"{name}_w"], z[f"{name}_b"]) for name, _, _ in NET_LAYERS})
+
+
+def set_proposal(ctx: Context, planes):
+    """Caller-supplied proposals (``amh_set_proposal``): planes is a
+    (ceil(H/2), ceil(W/2), 4) float32 array or CUDA tensor of (nx, ny, nz, d)
+    with n . X + d = 0 in reference-camera coordinates."""
+    L = lib()
+    L.amh_set_proposal.argtypes = [_vp, _vp, _i32, _i32, _i32]
+    if _is_torch(planes):
+        buf = planes.contiguous().float()
+        h2, w2 = int(buf.shape[0]), int(buf.shape[1])
+        rc = L.amh_set_proposal(ctx.ctx, _vp(buf.data_ptr()), w2, h2, AMH_MEM_DEVICE)
+    else:
+        buf = np.ascontiguousarray(planes, np.float32)
+        h2, w2 = buf.shape[0], buf.shape[1]
+        rc = L.amh_set_proposal(ctx.ctx, buf.ctypes.data, w2, h2, AMH_MEM_HOST)
+    ctx._check(rc)
+    ctx.synchronize()      # the copy has read buf before it goes out of scope
 
 
 def clear_proposal(ctx: Context):

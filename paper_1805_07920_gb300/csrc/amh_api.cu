@@ -95,6 +95,7 @@ void free_ctx(amh_ctx* c) {
   cudaFree(c->d_wmask);
   cudaFree(c->d_choice);
   cudaFree(c->d_pairs);
+  cudaFree(c->d_prop);
 }
 
 void fill_step_args(amh_ctx* c, int color) {
@@ -332,6 +333,29 @@ AMH_API int amh_select_sources(int32_t n_views, const amh_camera* cams, int32_t 
   const int n = std::min<int>(n_src, (int)cand.size());
   for (int i = 0; i < n; i++) src_out[i] = cand[i].second;
   *n_out = n;
+  return AMH_OK;
+}
+
+AMH_API int amh_set_proposal(amh_ctx* c, const float* plane4, int32_t width2, int32_t height2, int32_t mem) {
+  if (!c) return fail(nullptr, AMH_EINVAL, "amh_set_proposal: NULL context");
+  if (!plane4 || width2 < 1 || height2 < 1 || (mem != AMH_MEM_HOST && mem != AMH_MEM_DEVICE))
+    return fail(c, AMH_EINVAL, "amh_set_proposal: NULL planes, empty grid or bad memory kind");
+  const size_t cells = (size_t)width2 * height2;
+  if (cells > c->prop_cap) {
+    cudaFree(c->d_prop);
+    c->d_prop = nullptr;
+    c->prop_cap = 0;
+    const cudaError_t e = cudaMalloc(&c->d_prop, cells * sizeof(float4));
+    if (e != cudaSuccess) return fail(c, AMH_ENOMEM, "amh_set_proposal: %s", cudaGetErrorString(e));
+    c->prop_cap = cells;
+  }
+  const cudaError_t e = cudaMemcpyAsync(c->d_prop, plane4, cells * sizeof(float4),
+                                        mem == AMH_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                        c->stream);
+  if (e != cudaSuccess) return fail(c, AMH_ECUDA, "amh_set_proposal: %s", cudaGetErrorString(e));
+  c->args.prop = c->d_prop;
+  c->args.prop_w = width2;
+  c->args.prop_h = height2;
   return AMH_OK;
 }
 

@@ -23,6 +23,8 @@ struct amh_ctx {
   uint32_t* d_wmask = nullptr;
   uint8_t* d_choice = nullptr;
   unsigned long long* d_pairs = nullptr;  // amh::kPairCounters striped counters
+  float4* d_prop = nullptr;               // caller-set proposals (amh_set_proposal)
+  size_t prop_cap = 0;                    // cells d_prop holds
   amh::PhaseArgs args;
   int t = 0;
   bool initialized = false;

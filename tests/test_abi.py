@@ -132,6 +132,8 @@ def test_null_context_calls_fail_cleanly(built):
     assert L.amh_iterate(None, 1) == amh.AMH_EINVAL
     assert L.amh_default_params(None) == amh.AMH_EINVAL
     assert L.amh_synchronize(None) == amh.AMH_EINVAL
+    plane = (ctypes.c_float * 4)()
+    assert L.amh_set_proposal(None, plane, 1, 1, 0) == amh.AMH_EINVAL
     L.amh_destroy(None)
 
 
