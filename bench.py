@@ -365,7 +365,8 @@ def run_ours(args):
     extras = {}
     if not args.no_extras and world == 1:     # one-GPU measurements of the other forms
         if not args.texture_bilinear:
-            extras["texture_bilinear_3200x2112"] = bench_texture(sc, args.steps, phase_ms, ctx)
+            extras["texture_bilinear_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "texture")
+            extras["images_f16_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "f16")
         extras["batched_ring20"] = bench_batch(args, dist)
         extras["learned_proposal_1600x1056"] = bench_learned()
 
@@ -402,14 +403,20 @@ def run_ours(args):
     return 0
 
 
-def bench_texture(sc, steps, default_phase_ms, default_ctx):
-    """The same workload in the texture-filter precision form
-    (AMH_FLAG_TEXTURE_BILINEAR): throughput, phase-launch time, and the
-    fraction of pixels within 1 % of the ground truth next to the default
-    form's (both after the last timed step)."""
+def bench_form(sc, steps, default_phase_ms, default_ctx, form):
+    """The same workload in one of the precision forms -- "texture": the
+    texture unit's filter interpolates (AMH_FLAG_TEXTURE_BILINEAR); "f16": the
+    images stored as FP16 (AMH_FLAG_IMAGES_F16) -- : throughput, phase-launch
+    time, and the fraction of pixels within 1 % of the ground truth next to
+    the default form's (both after the last timed step)."""
     import torch
     from paper_1805_07920_gb300 import amh
-    ctx = amh.Context.from_scene(sc, seed=SEED, flags=amh.AMH_FLAG_TEXTURE_BILINEAR)
+    if form == "texture":
+        ctx = amh.Context.from_scene(sc, seed=SEED, flags=amh.AMH_FLAG_TEXTURE_BILINEAR)
+        what = "texture-unit linear filter (fractions and their product rounded to 1/256)"
+    else:
+        ctx = amh.Context.from_scene(sc, seed=SEED, images=[im.astype(np.float16) for im in sc.images])
+        what = "images stored as FP16 textures, FP32 interpolation and moments"
     stream = torch.cuda.current_stream()
     for _ in range(2):
         ctx.init_random()
@@ -443,8 +450,7 @@ def bench_texture(sc, steps, default_phase_ms, default_ctx):
     out = {"metric": METRIC, "unit": UNIT, "value": round(job_rate(sc.width * sc.height, ITERS, steps, 1, ms), 3),
            "ms_per_step": round(ms / steps, 3), "launch_ms": round(phase_ms, 3),
            "launch_ms_default_form": round(default_phase_ms, 3),
-           "accuracy_1pct": acc(ctx), "accuracy_1pct_default_form": acc(default_ctx),
-           "interpolation": "texture-unit linear filter (fractions and their product rounded to 1/256)"}
+           "accuracy_1pct": acc(ctx), "accuracy_1pct_default_form": acc(default_ctx), "form": what}
     ctx.close()
     return out
 
