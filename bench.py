@@ -96,9 +96,14 @@ def dist_setup(want_cuda: bool):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
+        import datetime
+
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl" if want_cuda else "gloo")
+        # a rank that dies or never arrives turns the others' next collective
+        # into an error after this long instead of a hang
+        timeout = datetime.timedelta(seconds=float(os.environ.get("AMH_DIST_TIMEOUT_S", "600")))
+        dist.init_process_group("nccl" if want_cuda else "gloo", timeout=timeout)
         pg = dist
     return rank, world, local, pg
 

@@ -143,3 +143,21 @@ def test_binding_has_no_cpu_fallback(tmp_path, monkeypatch):
     monkeypatch.setattr(amh, "_LIB", None)
     with pytest.raises(RuntimeError):
         amh.lib()
+
+
+def test_create_without_a_device_fails_cleanly(built):
+    """Valid arguments on a machine without a usable GPU: the first CUDA call
+    of amh_create fails, the partial context is freed and the error comes
+    back as a code and a message (no abort, no CPU path)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1805_07920_gb300 import amh
+    cams = _cams()
+    imgs = [np.zeros((12, 16), np.uint8) for _ in cams]
+    rc, msg, ctx = _create(cams, imgs, 0, [1, 2])
+    assert rc in (amh.AMH_ECUDA, amh.AMH_ENOMEM), (rc, msg)
+    assert "cuda" in msg.lower() and not ctx.value
+    # and again: nothing left behind makes a second attempt behave differently
+    rc2, msg2, ctx2 = _create(cams, imgs, 0, [1, 2])
+    assert rc2 == rc and not ctx2.value

@@ -2,7 +2,8 @@
 takes its own reference view of the same scene (no collective on the data
 path), the job time is the slowest rank's, and the rate counts every rank's
 pixels.  The GPU work itself needs no exchange, so nothing else crosses
-ranks."""
+ranks.  A rank that leaves between steps turns the survivors' next
+collective into an error within the group's timeout, not a hang."""
 import json
 import os
 import socket
@@ -57,3 +58,34 @@ def test_single_rank_needs_no_group():
     import bench
     assert bench.max_over_ranks(42.0, None, "cpu") == 42.0
     assert bench.job_rate(1000, 6, 2, 1, 1000.0) == pytest.approx(0.012)
+
+
+def _rank_leaves(rank, world, port, out_dir):
+    """Rank 1 joins the group and leaves before the timing exchange (between
+    steps, nothing in flight); rank 0 must get an error from it, in time."""
+    import time
+    sys.path.insert(0, REPO)
+    os.environ.update(WORLD_SIZE=str(world), RANK=str(rank), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port), AMH_DIST_TIMEOUT_S="10")
+    import bench
+    r, w, _, dist = bench.dist_setup(False)
+    if r == 1:
+        return                                   # leaves without the exchange
+    t0 = time.time()
+    try:
+        bench.max_over_ranks(100.0, dist, "cpu")
+        outcome = "completed"
+    except Exception as e:                       # the survivor sees the failure
+        outcome = f"error: {type(e).__name__}"
+    with open(os.path.join(out_dir, "rank0.json"), "w") as f:
+        json.dump({"outcome": outcome, "seconds": time.time() - t0}, f)
+
+
+def test_a_rank_that_leaves_is_detected(tmp_path):
+    mp = pytest.importorskip("torch.multiprocessing")
+    mp.start_processes(_rank_leaves, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    res = json.load(open(tmp_path / "rank0.json"))
+    assert res["outcome"].startswith("error"), res
+    assert res["seconds"] < 60, res
+
