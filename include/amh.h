@@ -54,7 +54,8 @@ enum {
   AMH_EINVAL = -1,      /* invalid argument (null pointer, size, camera, ...)   */
   AMH_ECUDA = -2,       /* a CUDA runtime call failed                            */
   AMH_ENOMEM = -3,      /* device or host allocation failed                      */
-  AMH_EDEVICE = -4,     /* a kernel reported an error through its status word   */
+  AMH_EDEVICE = -4,     /* a kernel reported an error through its status word
+                           (bounds-checked builds, see amh_bounds_checked)        */
   AMH_ESTATE = -5       /* call out of order (e.g. iterate before init)          */
 };
 
@@ -420,6 +421,15 @@ AMH_API const char* amh_last_error(const amh_ctx* ctx);
 
 /* Free everything; NULL is allowed. */
 AMH_API void amh_destroy(amh_ctx* ctx);
+
+/* 1 in a bounds-checked build of the library (compiled with
+ * -DAMH_BOUNDS_CHECK), else 0.  There every index the update computes into
+ * the state, the reference image or the proposals is checked; an index out
+ * of range is replaced by 0 and recorded in the context's (or batch's)
+ * status word, and amh_synchronize / amh_batch_synchronize return
+ * AMH_EDEVICE with the status in amh_last_error.  Results are otherwise the
+ * same as the normal build's. */
+AMH_API int amh_bounds_checked(void);
 
 #ifdef __cplusplus
 }

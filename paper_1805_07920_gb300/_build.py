@@ -54,24 +54,30 @@ def _run_all(cmds: list[list[str]], verbose: bool) -> None:
         raise RuntimeError(failed)
 
 
-def build(verbose: bool = False, extra_nvcc: list[str] | None = None) -> list[str]:
+def build(verbose: bool = False, extra_nvcc: list[str] | None = None, bounds_checked: bool = False) -> list[str]:
     """Compile every native library of the package; raise on any failure.
     Each CUDA source compiles to its own object at the same time as the
-    others (and the scene generator), then one link makes ``libamh.so``."""
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    others (and the scene generator), then one link makes ``libamh.so``.
+    ``bounds_checked`` builds ``libamh_checked.so`` instead: the same library
+    with -DAMH_BOUNDS_CHECK (every index of the update checked, see
+    amh_bounds_checked in include/amh.h)."""
+    obj_dir = OBJ_DIR + ("_checked" if bounds_checked else "")
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     flags = [*(extra_nvcc or []), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
              "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE]
+    if bounds_checked:
+        flags.append("-DAMH_BOUNDS_CHECK")
     objs, cmds = [], []
     for src in amh_sources():
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc, *flags, "-c", "-o", obj, src])
     sg = os.path.join(PKG_DIR, "synth", "scenegen.c")
     scenegen = os.path.join(LIB_DIR, "libscenegen.so")
     cmds.append(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", scenegen, sg, "-lm"])
     _run_all(cmds, verbose)
-    lib = os.path.join(LIB_DIR, "libamh.so")
+    lib = os.path.join(LIB_DIR, "libamh_checked.so" if bounds_checked else "libamh.so")
     _run_all([[nvcc, *ARCH, "-shared", "-o", lib, *objs]], verbose)
     return [lib, scenegen]
 

@@ -34,7 +34,7 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
            "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
            "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
-           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse", "amh_select_sources", "amh_set_proposal"]
+           "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse", "amh_select_sources", "amh_set_proposal", "amh_bounds_checked"]
 
 
 class AmhError(RuntimeError):

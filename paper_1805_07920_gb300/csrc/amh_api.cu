@@ -96,6 +96,7 @@ void free_ctx(amh_ctx* c) {
   cudaFree(c->d_choice);
   cudaFree(c->d_pairs);
   cudaFree(c->d_prop);
+  cudaFree(c->d_status);
 }
 
 void fill_step_args(amh_ctx* c, int color) {
@@ -210,6 +211,8 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   CTRY(cudaMalloc(&c->d_choice, np));
   CTRY(cudaMalloc(&c->d_pairs, kPairCounters * sizeof(unsigned long long)));
   CTRY(cudaMemsetAsync(c->d_pairs, 0, kPairCounters * sizeof(unsigned long long), c->stream));
+  CTRY(cudaMalloc(&c->d_status, sizeof(unsigned int)));
+  CTRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
 
   PhaseArgs& a = c->args;
   std::memset(&a, 0, sizeof a);
@@ -239,6 +242,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   a.vbest = c->d_vbest;
   a.wmask = c->d_wmask;
   a.choice = c->d_choice;
+  a.status = c->d_status;
   a.pairs = c->d_pairs;
 
   double RrT[9];
@@ -498,7 +502,21 @@ AMH_API int amh_pair_count(amh_ctx* c, uint64_t* count, int32_t reset) {
 AMH_API int amh_synchronize(amh_ctx* c) {
   if (!c) return AMH_EINVAL;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+#ifdef AMH_BOUNDS_CHECK
+  unsigned int st = 0;
+  CUDA_TRY(c, cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st) return fail(c, AMH_EDEVICE, "bounds check: index out of range in the update (status 0x%x: 1 pixel, 2 neighbour, "
+                                      "4 reference image, 8 proposal)", st);
+#endif
   return AMH_OK;
+}
+
+AMH_API int amh_bounds_checked(void) {
+#ifdef AMH_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 AMH_API const char* amh_last_error(const amh_ctx* c) {

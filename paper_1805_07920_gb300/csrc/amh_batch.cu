@@ -50,6 +50,7 @@ struct RefArgs {
   uint8_t* choice;
   const float4* prop;    // no learned proposals in the batched form (null)
   int prop_w, prop_h;
+  unsigned int* status;  // bounds-check status word of the batch
   const ViewConst* vt;   // N views in global memory
   int tile0, tiles_x, tiles;
   ViewConst v[kMaxSrc];  // copied from vt into shared memory per item
@@ -176,6 +177,7 @@ struct amh_batch {
   int init_items = 0;
   RefArgs* d_refs_init = nullptr;
   unsigned long long* d_pairs = nullptr;
+  unsigned int* d_status = nullptr;       // bounds-check status word (bounds-checked builds)
   int variant = 0;                        // tile width 16, 32, 64
   int t = 0;
   bool initialized = false;
@@ -247,6 +249,7 @@ void free_batch(amh_batch* b) {
   for (auto r : b->d_refs) cudaFree(r);
   cudaFree(b->d_refs_init);
   cudaFree(b->d_pairs);
+  cudaFree(b->d_status);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -415,6 +418,8 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
   CB(cudaMalloc(&b->d_choice, NP));
   CB(cudaMalloc(&b->d_pairs, kPairCounters * sizeof(unsigned long long)));
   CB(cudaMemsetAsync(b->d_pairs, 0, kPairCounters * sizeof(unsigned long long), b->stream));
+  CB(cudaMalloc(&b->d_status, sizeof(unsigned int)));
+  CB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), b->stream));
   for (int r = 0; r < n_refs; r++) {
     const amh_camera& cr = cams[refs[r]];
     double Kri[9];
@@ -451,6 +456,7 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
     ra.vbest = b->d_vbest + o;
     ra.wmask = b->d_wmask + o;
     ra.choice = b->d_choice + o;
+    ra.status = b->d_status;
     ra.tile0 = (int)views.size();   // temporarily: first view-table entry
     double RrT[9];
     for (int i = 0; i < 3; i++)
@@ -652,6 +658,11 @@ AMH_API int amh_batch_pair_count(amh_batch* b, uint64_t* count, int32_t reset) {
 AMH_API int amh_batch_synchronize(amh_batch* b) {
   if (!b) return AMH_EINVAL;
   BTRY(b, cudaStreamSynchronize(b->stream));
+#ifdef AMH_BOUNDS_CHECK
+  unsigned int st = 0;
+  BTRY(b, cudaMemcpy(&st, b->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st) return bfail(b, AMH_EDEVICE, "bounds check: index out of range in the update (status 0x%x)", st);
+#endif
   return AMH_OK;
 }
 

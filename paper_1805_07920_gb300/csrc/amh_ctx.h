@@ -24,6 +24,7 @@ struct amh_ctx {
   uint8_t* d_choice = nullptr;
   unsigned long long* d_pairs = nullptr;  // amh::kPairCounters striped counters
   float4* d_prop = nullptr;               // caller-set proposals (amh_set_proposal)
+  unsigned int* d_status = nullptr;       // bounds-check status word (bounds-checked builds)
   size_t prop_cap = 0;                    // cells d_prop holds
   amh::PhaseArgs args;
   int t = 0;

@@ -59,8 +59,28 @@ struct PhaseArgs {
   unsigned long long* pairs; // kPairCounters striped (hypothesis, view) evaluation counters
   const float4* prop;        // learned proposals (n, d) on the (x/2, y/2) grid, or null
   int prop_w, prop_h;
+  unsigned int* status;      // bounds-check status word (see checked_index)
   ViewConst v[kMaxSrc];
 };
+
+// Bounds-checked builds (compiled with -DAMH_BOUNDS_CHECK): every index the
+// update computes into the state, the reference image or the proposals is
+// checked; one out of range sets its bit in the status word and is replaced
+// by 0, so the access stays inside the array, and the host turns the word
+// into AMH_EDEVICE.  Other builds take the index as it is.
+enum : unsigned { kBadPixel = 1u, kBadNeighbour = 2u, kBadReference = 4u, kBadProposal = 8u };
+template <class A>
+__device__ __forceinline__ size_t checked_index(const A& a, size_t i, size_t n, unsigned code) {
+#ifdef AMH_BOUNDS_CHECK
+  if (i >= n) {
+    atomicOr(a.status, code);
+    return 0;
+  }
+#else
+  (void)a; (void)n; (void)code;
+#endif
+  return i;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32

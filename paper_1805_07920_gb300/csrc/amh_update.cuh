@@ -62,6 +62,7 @@ static_assert(kWinS % 2 == 0 && kWinN % 2 == 0, "window samples are processed in
 // intensity of reference pixel i (uint8 or FP16 images)
 template <bool kHalf, class A>
 __device__ __forceinline__ float ref_at(const A& a, size_t i) {
+  i = checked_index(a, i, (size_t)a.W * a.H, kBadReference);
   if (kHalf) return __half2float(__ldg(reinterpret_cast<const __half*>(a.ref) + i));
   return (float)__ldg(reinterpret_cast<const uint8_t*>(a.ref) + i);
 }
@@ -383,7 +384,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
                                              int* npairs) {
   constexpr bool kTex = (kMode & kTexture) != 0;
   const int N = a.N;
-  const size_t pi = (size_t)y * a.W + x;
+  const size_t pi = checked_index(a, (size_t)y * a.W + x, (size_t)a.W * a.H, kBadPixel);
   const float fx = (float)x, fy = (float)y;
   const float3 ray = ref_ray(a.Kinv, fx, fy);
 
@@ -395,14 +396,15 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     if (kMode & kSymmetric) {
       const int dist = g < 4 ? 1 : 5, dir = g & 3;
       const int qx = x + (dir == 2 ? -dist : dir == 3 ? dist : 0), qy = y + (dir == 0 ? -dist : dir == 1 ? dist : 0);
-      if (qx >= 0 && qy >= 0 && qx < a.W && qy < a.H) best = qy * a.W + qx;
+      if (qx >= 0 && qy >= 0 && qx < a.W && qy < a.H)
+        best = (int)checked_index(a, (size_t)qy * a.W + qx, (size_t)a.W * a.H, kBadNeighbour);
     } else {
       float bc = 0.f;
 #pragma unroll
       for (int c = acp_start(g); c < acp_start(g + 1); c++) {
         const int qx = x + acp_dx(c), qy = y + acp_dy(c);
         if (qx < 0 || qy < 0 || qx >= a.W || qy >= a.H) continue;
-        const int q = qy * a.W + qx;
+        const int q = (int)checked_index(a, (size_t)qy * a.W + qx, (size_t)a.W * a.H, kBadNeighbour);
         const float cq = __ldg(&a.cost[q]);
         if (best < 0 || cq < bc) { best = q; bc = cq; }
       }
@@ -544,7 +546,8 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   float4 prop = make_float4(0.f, 0.f, 0.f, 0.f);
   bool has_prop = false;
   if (a.prop) {
-    const float4 pr = a.prop[(size_t)min(y / 2, a.prop_h - 1) * a.prop_w + min(x / 2, a.prop_w - 1)];
+    const float4 pr = a.prop[checked_index(a, (size_t)min(y / 2, a.prop_h - 1) * a.prop_w + min(x / 2, a.prop_w - 1),
+                                           (size_t)a.prop_w * a.prop_h, kBadProposal)];
     const float den = pr.x * ray.x + pr.y * ray.y + pr.z * ray.z;
     const float Dx = den < 0.f ? -pr.w / den : 0.f;
     has_prop = pr.w > 0.f && Dx > 0.f && isfinite(Dx);
@@ -595,7 +598,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 template <bool kHalf, bool kTex, class A>
 __device__ __forceinline__ void init_pixel(const A& a, PixelArrays& sm, int x, int y, int* npairs) {
   const int N = a.N;
-  const size_t pi = (size_t)y * a.W + x;
+  const size_t pi = checked_index(a, (size_t)y * a.W + x, (size_t)a.W * a.H, kBadPixel);
   const float fx = (float)x, fy = (float)y;
   const float3 ray = ref_ray(a.Kinv, fx, fy);
   const uint4 r = philox4x32_10(make_uint4((uint32_t)pi, 0u, 0u, 0u), a.key0, a.key1);
