@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -191,6 +192,15 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     delete c;
     return code;
   };
+  // Fault injection for tests: with AMH_FAIL_ALLOC_AT=k in the environment,
+  // the k-th device allocation of this call reports an out-of-memory error
+  // without allocating, so the cleanup path of a real failure runs.
+  int alloc_n = 0, alloc_fail_at = 0;
+  if (const char* e = std::getenv("AMH_FAIL_ALLOC_AT")) alloc_fail_at = std::atoi(e);
+  auto injected = [&]() { return alloc_fail_at > 0 && ++alloc_n == alloc_fail_at; };
+  auto dev_alloc = [&](void** ptr, size_t bytes) {
+    return injected() ? cudaErrorMemoryAllocation : cudaMalloc(ptr, bytes);
+  };
 #define CTRY(call)                                                                              \
   do {                                                                                          \
     cudaError_t e_ = (call);                                                                    \
@@ -201,17 +211,17 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     }                                                                                           \
   } while (0)
 
-  CTRY(cudaMalloc(&c->d_ref, np * es));
+  CTRY(dev_alloc((void**)&c->d_ref, np * es));
   CTRY(cudaMemcpyAsync(c->d_ref, images[ref], np * es, kind, c->stream));
-  CTRY(cudaMalloc(&c->d_plane, np * sizeof(float4)));
-  CTRY(cudaMalloc(&c->d_cost, np * sizeof(float)));
-  CTRY(cudaMalloc(&c->d_sel, np * sizeof(uint32_t)));
-  CTRY(cudaMalloc(&c->d_vbest, np));
-  CTRY(cudaMalloc(&c->d_wmask, np * sizeof(uint32_t)));
-  CTRY(cudaMalloc(&c->d_choice, np));
-  CTRY(cudaMalloc(&c->d_pairs, kPairCounters * sizeof(unsigned long long)));
+  CTRY(dev_alloc((void**)&c->d_plane, np * sizeof(float4)));
+  CTRY(dev_alloc((void**)&c->d_cost, np * sizeof(float)));
+  CTRY(dev_alloc((void**)&c->d_sel, np * sizeof(uint32_t)));
+  CTRY(dev_alloc((void**)&c->d_vbest, np));
+  CTRY(dev_alloc((void**)&c->d_wmask, np * sizeof(uint32_t)));
+  CTRY(dev_alloc((void**)&c->d_choice, np));
+  CTRY(dev_alloc((void**)&c->d_pairs, kPairCounters * sizeof(unsigned long long)));
   CTRY(cudaMemsetAsync(c->d_pairs, 0, kPairCounters * sizeof(unsigned long long), c->stream));
-  CTRY(cudaMalloc(&c->d_status, sizeof(unsigned int)));
+  CTRY(dev_alloc((void**)&c->d_status, sizeof(unsigned int)));
   CTRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
 
   PhaseArgs& a = c->args;
@@ -273,7 +283,8 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     // read as the value; point sampling (the kernels gather 2 x 2 texels and
     // blend in FP32) or, for AMH_FLAG_TEXTURE_BILINEAR, the linear filter
     cudaChannelFormatDesc fd = half ? cudaCreateChannelDescHalf() : cudaCreateChannelDesc<uint8_t>();
-    CTRY(cudaMallocArray(&c->arr[j], &fd, cj.width, cj.height, cudaArrayTextureGather));
+    CTRY(injected() ? cudaErrorMemoryAllocation
+                    : cudaMallocArray(&c->arr[j], &fd, cj.width, cj.height, cudaArrayTextureGather));
     CTRY(cudaMemcpy2DToArrayAsync(c->arr[j], 0, 0, images[v], cj.width * es, cj.width * es, cj.height, kind,
                                   c->stream));
     cudaResourceDesc rd;
