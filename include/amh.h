@@ -122,7 +122,8 @@ typedef struct {
  *   wmask[W H]    uint32 views with a nonzero weight psi_mod at the last update
  *   choice[W H]   uint8  row that won the last update: 0..7 ACP region
  *                        (near up/down/left/right, far up/down/left/right),
- *                        8 own plane, 9 + c refinement candidate c
+ *                        8 own plane, 9 + c refinement candidate c,
+ *                        15 a proposal (amh_net_propose / amh_set_proposal)
  *   t             iteration index of the next update (0-based)
  * Any pointer except plane may be NULL in amh_get_state (not read back) and
  * in amh_set_state (left unchanged; plane is required there). */
@@ -145,8 +146,11 @@ AMH_API int amh_default_params(amh_params* out);
  * memory kind `images_mem`; only ref and the listed sources are read.  The
  * images are copied into device-resident texture arrays.  Fails with
  * AMH_EINVAL on bad sizes, singular or non-pinhole K, or unsupported window
- * parameters; with AMH_ENOMEM when the device is full.  `stream` is a
- * cudaStream_t (NULL = legacy default stream). */
+ * parameters; with AMH_ENOMEM when the device is full, after freeing what
+ * it had allocated.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream).  Test facility: with AMH_FAIL_ALLOC_AT=k in the environment the
+ * k-th device allocation of the call reports out-of-memory without
+ * allocating. */
 AMH_API int amh_create(amh_ctx** out, const amh_params* params, int32_t n_views,
                        const amh_camera* cams, const uint8_t* const* images,
                        int32_t images_mem, int32_t ref, const int32_t* src,
