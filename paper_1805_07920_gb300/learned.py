@@ -129,7 +129,7 @@ def make_examples(seeds, width, height, log=print):
     return ex, (w2, h2)
 
 
-def train(out_dir, n_scenes=200, width=800, height=528, steps=8000, lr=1e-3, seed=0, log=print):
+def train(out_dir, n_scenes=200, width=1600, height=1056, steps=8000, lr=1e-3, seed=0, log=print):
     os.makedirs(out_dir, exist_ok=True)
     log(f"rendering {n_scenes} training scenes at {width}x{height}, plain method states after {T_IN} -> {T_FINAL}")
     train_ex, (w2, h2) = make_examples(range(TRAIN_SEED0, TRAIN_SEED0 + n_scenes), width, height, log)
@@ -262,8 +262,8 @@ def main(argv=None):
     t = sub.add_parser("train")
     t.add_argument("--out", required=True)
     t.add_argument("--scenes", type=int, default=200)
-    t.add_argument("--width", type=int, default=800)
-    t.add_argument("--height", type=int, default=528)
+    t.add_argument("--width", type=int, default=1600)
+    t.add_argument("--height", type=int, default=1056)
     t.add_argument("--steps", type=int, default=8000)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--eval", action="store_true", help="evaluate on the held-out scenes afterwards")

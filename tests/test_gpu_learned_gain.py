@@ -2,9 +2,10 @@
 
 The committed weights (paper_1805_07920_gb300/weights/proposal_net.npz) were
 trained by the library's own kernels on the plain method's outputs for 200
-seeded 800x528 scenes (seeds 1000-1199; validation 1900-1905) and the
+seeded 1600x1056 scenes (seeds 1000-1199; validation 1900-1905) and the
 proposal schedule (network on the state after 2 iterations, its plane scored
-during the third) was picked on scenes 2000-2002.  Here two further held-out
+during the third) and the training resolution were picked on scenes
+2000-2002.  Here two further held-out
 scenes at 1600x1056 with 10 sources (seeds 2003, 2004) are run with and
 without the proposal from the same random initialisation.  Accuracy is the
 fraction of valid pixels with depth within 1 % of the ground truth (valid:
