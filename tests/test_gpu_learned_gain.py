@@ -13,7 +13,7 @@ ground truth present, >= 5 px from the border).
 
 Shown: from the injected iteration on the learned run is never behind the
 plain one, it ends ahead, and it reaches the plain method's 6-iteration
-accuracy in fewer iterations on at least one scene (the device times of both
+accuracy in fewer iterations on both scenes (the device times of both
 paths, network included, are printed)."""
 import numpy as np
 import pytest
@@ -50,4 +50,4 @@ def test_trained_network_gain(amh, synth_mod):
         assert (al[2:] >= ap[2:] - 1e-4).all()
         assert al[-1] > ap[-1]
         iters_to.append(s["iters_to_plain_final"] or 99)
-    assert min(iters_to) <= 5
+    assert max(iters_to) <= 5          # fewer iterations than the plain method's 6 on both scenes
