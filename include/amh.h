@@ -362,7 +362,7 @@ AMH_API int amh_read_maps_noalloc(amh_ctx* ctx, float* depth, float* normal3,
  * follow Gipuma, the paper's reference [9], under these readings).  Both
  * calls take DEVICE buffers the caller owns and run asynchronously on
  * `stream`; errors: AMH_EINVAL for NULL / aliased buffers or bad sizes,
- * AMH_ECUDA for a failed launch.
+ * AMH_ECUDA for a failed launch, each with a message in amh_last_error(NULL).
  * ------------------------------------------------------------------------ */
 /* 4x4 median of a width x height depth map: the window holds the offsets
  * -2..+1 in x and y (clamped at the borders), the value is the mean of its

@@ -134,7 +134,7 @@ def median4(depth):
     L.amh_median4.argtypes = [_vp, _vp, _i32, _i32, _vp]
     rc = L.amh_median4(_vp(d.data_ptr()), _vp(out.data_ptr()), d.shape[1], d.shape[0], _current_stream())
     if rc != AMH_OK:
-        raise AmhError(rc, "amh_median4 failed")
+        raise AmhError(rc, L.amh_last_error(None).decode())
     return out
 
 
@@ -161,7 +161,7 @@ def fuse(cams, depths, normals, f_eps=0.3, f_ang_deg=30.0, f_con=2):
     L.amh_fuse.argtypes = [_i32, ctypes.POINTER(Camera), _vp, _vp, ctypes.c_float, ctypes.c_float, _i32, _vp, _vp, _vp]
     rc = L.amh_fuse(V, arr, P(d), P(n), float(f_eps), float(f_ang_deg), int(f_con), P(pts), P(cnt), _current_stream())
     if rc != AMH_OK:
-        raise AmhError(rc, "amh_fuse failed")
+        raise AmhError(rc, L.amh_last_error(None).decode())
     return pts, cnt
 
 

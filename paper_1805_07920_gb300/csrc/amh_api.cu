@@ -50,6 +50,19 @@ int fail(amh_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+}  // namespace
+
+int amh::fail_no_context(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_create_err = buf;
+  return code;
+}
+
+namespace {
 #define CUDA_TRY(ctx, call)                                                                 \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \

@@ -31,3 +31,11 @@ struct amh_ctx {
   bool initialized = false;
   std::string err;
 };
+
+namespace amh {
+// Message for amh_last_error(NULL): the last failure of a call that has no
+// context (amh_create, amh_median4, amh_fuse, amh_select_sources) on this
+// host thread.  Returns code.
+int fail_no_context(int code, const char* fmt, ...);
+}  // namespace amh
+

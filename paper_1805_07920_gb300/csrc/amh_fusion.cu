@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "amh.h"
+#include "amh_ctx.h"
 
 namespace amh {
 namespace {
@@ -156,7 +157,10 @@ bool inv3f(const double* A, double* I) {
   return true;
 }
 
-int launch_status() { return cudaGetLastError() == cudaSuccess ? AMH_OK : AMH_ECUDA; }
+int launch_status(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? AMH_OK : fail_no_context(AMH_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+}
 
 }  // namespace
 }  // namespace amh
@@ -166,18 +170,21 @@ using namespace amh;
 extern "C" {
 
 AMH_API int amh_median4(const float* depth_in, float* depth_out, int32_t width, int32_t height, void* stream) {
-  if (!depth_in || !depth_out || width < 1 || height < 1 || depth_in == depth_out) return AMH_EINVAL;
+  if (!depth_in || !depth_out || width < 1 || height < 1 || depth_in == depth_out)
+    return fail_no_context(AMH_EINVAL, "amh_median4: NULL or aliased buffers, or an empty image");
   const size_t n = (size_t)width * height;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 65535);
   median4_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(depth_in, depth_out, width, height);
-  return launch_status();
+  return launch_status("amh_median4");
 }
 
 AMH_API int amh_fuse(int32_t n_views, const amh_camera* cams, const float* const* depth, const float* const* normal3,
                      float f_eps, float f_ang_deg, int32_t f_con, float* const* points6, uint8_t* const* count,
                      void* stream) {
-  if (n_views < 2 || n_views > kFuseMaxViews || !cams || !depth || !normal3 || !points6 || !count) return AMH_EINVAL;
-  if (!(f_eps >= 0.f) || !(f_ang_deg >= 0.f && f_ang_deg <= 180.f) || f_con < 1) return AMH_EINVAL;
+  if (n_views < 2 || n_views > kFuseMaxViews || !cams || !depth || !normal3 || !points6 || !count)
+    return fail_no_context(AMH_EINVAL, "amh_fuse: 2..%d views with non-NULL arrays required", kFuseMaxViews);
+  if (!(f_eps >= 0.f) || !(f_ang_deg >= 0.f && f_ang_deg <= 180.f) || f_con < 1)
+    return fail_no_context(AMH_EINVAL, "amh_fuse: thresholds out of range");
   FuseArgs a;
   std::memset(&a, 0, sizeof a);
   a.n = n_views;
@@ -187,9 +194,10 @@ AMH_API int amh_fuse(int32_t n_views, const amh_camera* cams, const float* const
   size_t most = 0;
   for (int v = 0; v < n_views; v++) {
     const amh_camera& c = cams[v];
-    if (!depth[v] || !normal3[v] || !points6[v] || !count[v] || c.width < 1 || c.height < 1) return AMH_EINVAL;
+    if (!depth[v] || !normal3[v] || !points6[v] || !count[v] || c.width < 1 || c.height < 1)
+      return fail_no_context(AMH_EINVAL, "amh_fuse: view %d has a NULL array or an empty image", v);
     double Ki[9];
-    if (!inv3f(c.K, Ki)) return AMH_EINVAL;
+    if (!inv3f(c.K, Ki)) return fail_no_context(AMH_EINVAL, "amh_fuse: K of view %d is singular", v);
     FuseView& F = a.v[v];
     for (int k = 0; k < 9; k++) {
       F.Kinv[k] = (float)Ki[k];
@@ -210,7 +218,7 @@ AMH_API int amh_fuse(int32_t n_views, const amh_camera* cams, const float* const
   }
   dim3 grid((unsigned)std::min<size_t>((most + 255) / 256, 4096), (unsigned)n_views);
   fuse_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-  return launch_status();
+  return launch_status("amh_fuse");
 }
 
 }  // extern "C"

@@ -161,3 +161,14 @@ def test_create_without_a_device_fails_cleanly(built):
     # and again: nothing left behind makes a second attempt behave differently
     rc2, msg2, ctx2 = _create(cams, imgs, 0, [1, 2])
     assert rc2 == rc and not ctx2.value
+
+
+def test_post_processing_argument_errors_carry_a_message(built):
+    from paper_1805_07920_gb300 import amh
+    L = amh.lib()
+    L.amh_last_error.restype = ctypes.c_char_p
+    assert L.amh_median4(None, None, 4, 4, None) == amh.AMH_EINVAL
+    assert b"amh_median4" in L.amh_last_error(None)
+    assert L.amh_fuse(1, None, None, None, ctypes.c_float(0.3), ctypes.c_float(30.0), 2, None, None, None) == amh.AMH_EINVAL
+    assert b"amh_fuse" in L.amh_last_error(None)
+
