@@ -76,3 +76,35 @@ def test_stricter_consensus_keeps_a_subset(fusion_scene):
     vc = F.fuse(sc.cams, D, N, f_con=4)[1]
     for a, b, c in zip(va, vb, vc):
         assert (b <= a).all() and (c <= b).all() and c.sum() < a.sum()
+
+
+def _pair_cams(synth_mod, b, W=64, H=48, f=100.0):
+    K = np.array([[f, 0.0, (W - 1) / 2], [0.0, f, (H - 1) / 2], [0.0, 0.0, 1.0]])
+    R = np.eye(3)
+    return [synth_mod.Camera(K, R, np.zeros(3), W, H),
+            synth_mod.Camera(K, R, np.array([-b, 0.0, 0.0]), W, H)]   # centre (b, 0, 0)
+
+
+def test_fronto_parallel_pair_closed_form(synth_mod):
+    """Two cameras with the same orientation, centres b apart along x, a
+    fronto-parallel plane: view 0 sees it at depth 5, view 1 (slightly off) at
+    5.05.  View 0's pixel x lands on view 1's pixel x - 20 b exactly (f = 100),
+    where the disparity difference is f b |1/5 - 1/5.05| = 0.198 b: one
+    agreeing view for b = 1 (a fused point halfway, at depth 5.025), none for
+    b = 2 (0.396 > f_eps = 0.3)."""
+    W, H = 64, 48
+    D = [np.full((H, W), 5.0), np.full((H, W), 5.05)]
+    N = [np.tile(np.array([0.0, 0.0, -1.0]), (H, W, 1))] * 2
+    pts, valid, cnt, amb = F.fuse(_pair_cams(synth_mod, 1.0), D, N, f_eps=0.3, f_ang_deg=30.0, f_con=1)
+    xs = np.arange(W)
+    seen = np.broadcast_to(xs >= 20, (H, W))               # x - 20 inside view 1
+    assert not amb[0].any()
+    np.testing.assert_array_equal(cnt[0], seen.astype(cnt[0].dtype))
+    np.testing.assert_array_equal(valid[0], seen)
+    np.testing.assert_allclose(pts[0][..., 2][seen], 5.025, rtol=0, atol=1e-12)
+    X0 = 5.0 * (xs - (W - 1) / 2) / 100.0                    # view 0's point
+    X1 = 5.05 * (xs - 20 - (W - 1) / 2) / 100.0 + 1.0        # view 1's point at x - 20
+    np.testing.assert_allclose(pts[0][..., 0][seen], np.broadcast_to(0.5 * (X0 + X1), (H, W))[seen], atol=1e-12)
+    # twice the baseline: the same depth offset is twice the disparity, rejected
+    _, valid2, cnt2, _ = F.fuse(_pair_cams(synth_mod, 2.0), D, N, f_eps=0.3, f_ang_deg=30.0, f_con=1)
+    assert not valid2[0].any() and not cnt2[0].any()

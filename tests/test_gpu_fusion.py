@@ -81,3 +81,24 @@ def test_fusion_of_estimated_maps(amh, synth_mod):
     res = _fuse_both(amh, sc, D, N)
     _check(res, D)
     assert np.mean([v.mean() for v in res[3]]) > 0.5      # most pixels fuse
+
+
+@pytest.mark.parametrize("baseline,agree", [(1.0, True), (2.0, False)])
+def test_fusion_fronto_parallel_pair(amh, synth_mod, baseline, agree):
+    """The closed-form pair of the oracle's pins (same orientation, centres
+    `baseline` apart, depths 5 and 5.05 on a fronto-parallel plane): one
+    agreeing view and fused points at depth 5.025 for baseline 1, none for 2."""
+    import torch
+    W, H, f = 64, 48, 100.0
+    K = np.array([[f, 0.0, (W - 1) / 2], [0.0, f, (H - 1) / 2], [0.0, 0.0, 1.0]])
+    cams = [synth_mod.Camera(K, np.eye(3), np.zeros(3), W, H),
+            synth_mod.Camera(K, np.eye(3), np.array([-baseline, 0.0, 0.0]), W, H)]
+    D = [np.full((H, W), 5.0, np.float32), np.full((H, W), 5.05, np.float32)]
+    N = [np.tile(np.array([0.0, 0.0, -1.0], np.float32), (H, W, 1))] * 2
+    pts, cnt = amh.fuse(cams, [torch.from_numpy(d).cuda() for d in D], [torch.from_numpy(n).cuda() for n in N],
+                        f_con=1)
+    c0 = cnt[0].cpu().numpy()
+    seen = np.broadcast_to(np.arange(W) >= 20 * baseline, (H, W)) if agree else np.zeros((H, W), bool)
+    np.testing.assert_array_equal(c0, seen.astype(np.uint8))
+    if agree:
+        np.testing.assert_allclose(pts[0].cpu().numpy()[..., 2][seen], 5.025, rtol=1e-6)
