@@ -334,10 +334,11 @@ AMH_API void amh_net_destroy(amh_net* net);
 
 /* amh_read_maps without any allocation (the paper has no counterpart: this
  * is a service for callers that cannot allocate device memory when they read
- * results -- code running while a stream is captured into a CUDA graph,
- * where allocation calls are not allowed; hosts whose pooling allocator owns
- * the GPU and forbids other device allocations; loops that must not allocate
- * after start-up).
+ * results -- hosts whose pooling allocator owns the GPU and forbids any other
+ * device allocation, and loops that must not allocate after start-up, where
+ * amh_read_maps with host buffers would allocate a staging buffer per call).
+ * It is a plain blocking read: it synchronises the context's stream and copies
+ * into pageable host memory, so it must be called outside stream capture.
  *
  * Copies the depth (float per pixel) and/or the normal (3 floats per pixel)
  * of the pixels [first_pixel, first_pixel + n_pixels) in row-major order into
@@ -348,12 +349,14 @@ AMH_API void amh_net_destroy(amh_net* net);
  *
  * The data is staged through one fixed scratch array that is part of the
  * library's device image (4 MB, held on every GPU that loads the library
- * until the process exits); the call makes no cudaMalloc/cudaFree or other
- * allocating call.  The first call on a device looks up the array's device
- * address (once per device); make that first call before any stream capture.
- * Every call on a device shares the one array: calls whose GPU work can
- * overlap (other streams, other host threads) race on it, so serialise them.
- * The call synchronises the context's stream before it returns. */
+ * until the process exits); the call itself makes no cudaMalloc/cudaFree or
+ * other allocating call.  The first call on a device looks up the array's
+ * device address (once per device, on the device the context was created
+ * on); that first call may also load the library's kernels onto the device,
+ * which the CUDA runtime does lazily and which can reserve device memory of
+ * its own.  Every call on a device shares the one array: calls whose GPU work
+ * can overlap (other streams, other host threads) race on it, so serialise
+ * them.  The call synchronises the context's stream before it returns. */
 AMH_API int amh_read_maps_noalloc(amh_ctx* ctx, float* depth, float* normal3,
                                   int64_t first_pixel, int64_t n_pixels);
 

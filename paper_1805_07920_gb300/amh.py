@@ -332,11 +332,24 @@ class Context:
 
     def read_maps_noalloc(self, depth=None, normal=None, first_pixel: int = 0, n_pixels: int | None = None):
         """Depth/normal of a pixel range into host arrays, without any device
-        allocation (amh_read_maps_noalloc; at most NOALLOC_MAX_PIXELS)."""
+        allocation (amh_read_maps_noalloc; at most NOALLOC_MAX_PIXELS per
+        call).  depth / normal must be C-contiguous float32 numpy arrays of at
+        least n_pixels / 3 * n_pixels elements.  Without n_pixels the call
+        reads as many pixels from first_pixel on as remain in the image, fit
+        the per-call maximum and fit the given arrays."""
+        bufs = [(name, a, per) for name, a, per in (("depth", depth, 1), ("normal", normal, 3)) if a is not None]
+        for name, a, _ in bufs:
+            if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"read_maps_noalloc: {name} must be a C-contiguous float32 numpy array")
         if n_pixels is None:
-            n_pixels = self.W * self.H - first_pixel
+            n_pixels = min([self.W * self.H - int(first_pixel), NOALLOC_MAX_PIXELS] +
+                           [a.size // per for _, a, per in bufs])
+        n_pixels = int(n_pixels)
+        for name, a, per in bufs:
+            if a.size < per * max(n_pixels, 0):
+                raise ValueError(f"read_maps_noalloc: {name} holds {a.size} floats, {per * n_pixels} needed")
         self._check(lib().amh_read_maps_noalloc(self.ctx, _ptr(depth), _ptr(normal), int(first_pixel),
-                                                int(n_pixels)))
+                                                n_pixels))
 
     def read_maps_device(self, depth=None, normal=None, cost=None, selected=None):
         self._check(lib().amh_read_maps(self.ctx, _ptr(depth), _ptr(normal), _ptr(cost), _ptr(selected),

@@ -187,6 +187,13 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   if (!c) return fail(nullptr, AMH_ENOMEM, "host allocation failed");
   c->p = *p;
   c->ref = ref;
+  {
+    const cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, AMH_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+  }
   c->N = n_src;
   c->stream = (cudaStream_t)stream;
   const amh_camera& cr = cams[ref];

@@ -11,6 +11,7 @@
 struct amh_ctx {
   amh_params p;
   int W = 0, H = 0, N = 0, ref = 0;
+  int device = 0;                         // the CUDA device current at amh_create
   int src[AMH_MAX_SRC];
   cudaStream_t stream = nullptr;
   cudaArray_t arr[AMH_MAX_SRC] = {};      // source views, uint8 texture arrays

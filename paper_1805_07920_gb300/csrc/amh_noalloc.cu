@@ -2,12 +2,12 @@
 //
 // amh_read_maps() with host buffers stages the depth and normal maps in a
 // device buffer it allocates for the call.  Some callers cannot allocate
-// device memory at that point: code running while a stream is being captured
-// into a CUDA graph (allocation calls are not allowed there), hosts that hand
-// the GPU to a pooling allocator and forbid any other device allocation, and
-// real-time loops that must not allocate after start-up.  This variant stages
-// through one fixed scratch array that is part of the library's device image
-// instead.
+// device memory at that point: hosts that hand the GPU to a pooling allocator
+// and forbid any other device allocation, and real-time loops that must not
+// allocate after start-up.  This variant stages through one fixed scratch
+// array that is part of the library's device image instead.  It blocks (it
+// synchronises the context's stream and copies into pageable host memory), so
+// it is called outside stream capture.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -64,12 +64,11 @@ extern "C" AMH_API int amh_read_maps_noalloc(amh_ctx* c, float* depth, float* no
                    "read larger maps in slices");
   if (n_pixels == 0) return AMH_OK;
 
-  // the context's device, made current for the set-up and the launch
-  cudaPointerAttributes attr;
-  cudaError_t e = cudaPointerGetAttributes(&attr, c->d_plane);
-  if (e != cudaSuccess) return set_err(c, AMH_ECUDA, "amh_read_maps_noalloc: device of the context", e);
-  const int dev = attr.device;
+  // the context's device (recorded at amh_create), made current for the
+  // set-up and the launch
+  const int dev = c->device;
   if (dev < 0 || dev >= kMaxDevices) return set_err(c, AMH_EINVAL, "amh_read_maps_noalloc: device index too large");
+  cudaError_t e;
   int prev = 0;
   e = cudaGetDevice(&prev);
   if (e != cudaSuccess) return set_err(c, AMH_ECUDA, "amh_read_maps_noalloc: cudaGetDevice", e);

@@ -505,6 +505,37 @@ def test_refinement_candidates(oracle_mod):
             assert c[5, 3] == 4.0
 
 
+def test_refinement_range_is_reached_on_both_sides(oracle_mod):
+    """Two-sided pin of the bisection range rho_t = 2^-(t+1) of Sec. 3.3 (the
+    range that halves every iteration, starting at one half): over every
+    pixel of a 40 x 36 image (1440 independent draws per t) the perturbed
+    depth D (1 + rho u), u uniform in (-1, 1), must fill the range on both
+    sides -- its extremes beyond 0.9 rho above and below -- and never leave
+    it; the perturbed normal n + rho delta (delta uniform in the unit cube)
+    must turn further from n than any box of half-width rho / 2 allows
+    (asin(sqrt(3) rho / 2): the ball around such a box), and never further
+    than the rho box allows.  A range off by a factor of two either way
+    fails one side."""
+    o = _flat_scene(oracle_mod)
+    n0 = np.array([0.2, -0.1, -1.0])
+    n0 /= np.linalg.norm(n0)
+    D0 = 4.0
+    pl = np.array([*n0, D0])
+    for t in range(6):
+        rho = 2.0 ** -(t + 1)
+        rel, ang = [], []
+        for y in range(o.H):
+            for x in range(o.W):
+                c = o.refine_candidates(x, y, pl, t)[0]
+                rel.append(c[3] / D0 - 1.0)
+                ang.append(math.acos(min(1.0, abs(float(c[:3] @ n0)))))
+        rel, ang = np.array(rel), np.array(ang)
+        assert rel.max() > 0.9 * rho and rel.min() < -0.9 * rho, (t, rel.min(), rel.max())
+        assert np.abs(rel).max() <= rho * (1 + 1e-12), t
+        assert ang.max() > math.asin(min(1.0, math.sqrt(3) * rho / 2)), (t, ang.max())
+        assert ang.max() <= math.asin(min(1.0, math.sqrt(3) * rho)) + 1e-12, (t, ang.max())
+
+
 # --------------------------------------------------------------------------
 # the checkerboard phase as a whole
 # --------------------------------------------------------------------------

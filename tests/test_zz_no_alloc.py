@@ -1,7 +1,9 @@
 """amh_read_maps_noalloc: the map read-back for callers that cannot allocate
-device memory when they read results (stream capture, a pooling allocator
-that owns the GPU, allocation-free loops).  It must return exactly what
-amh_read_maps returns, call after call, through the C-ABI.
+device memory when they read results (a pooling allocator that owns the GPU,
+loops that must not allocate after start-up).  It is a blocking read, made
+outside stream capture.  It must return exactly what amh_read_maps returns,
+call after call, through the C-ABI, and leave the device's free memory
+where it was.
 
 Kept in a file of its own, collected last."""
 import numpy as np
@@ -79,3 +81,44 @@ def test_noalloc_rejects_oversize_and_bad_ranges(amh, synth_mod):
     d = np.empty(10, np.float32)
     g.read_maps_noalloc(d, None, 0, 10)
     np.testing.assert_array_equal(d, g.read_maps()["depth"].ravel()[:10])
+
+
+def test_noalloc_leaves_device_memory_unchanged(amh, synth_mod):
+    """After a first call (which looks up the scratch array and may load the
+    library's kernels), further calls change the device's free memory by
+    nothing: no staging buffer is allocated."""
+    import torch
+    sc = synth_mod.make_scene("tiny")
+    g = amh.Context.from_scene(sc, seed=20)
+    g.init_random()
+    g.iterate(1)
+    n = sc.width * sc.height
+    d = np.empty(n, np.float32)
+    nm = np.empty((n, 3), np.float32)
+    g.read_maps_noalloc(d, nm, 0, n)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        g.read_maps_noalloc(d, nm, 0, n)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    np.testing.assert_array_equal(d, g.read_maps()["depth"].ravel())
+
+
+def test_noalloc_binding_checks_buffers(amh, synth_mod):
+    """The binding refuses buffers the C call would overrun or misread."""
+    sc = synth_mod.make_scene("tiny")
+    g = amh.Context.from_scene(sc, seed=21)
+    g.init_random()
+    with pytest.raises(ValueError):
+        g.read_maps_noalloc(np.empty(10, np.float64), None, 0, 10)         # wrong dtype
+    with pytest.raises(ValueError):
+        g.read_maps_noalloc(np.empty(9, np.float32), None, 0, 10)          # too short
+    with pytest.raises(ValueError):
+        g.read_maps_noalloc(None, np.empty((9, 3), np.float32), 0, 10)     # normals too short
+    with pytest.raises(ValueError):
+        g.read_maps_noalloc(np.empty((20, 2), np.float32)[:, 0], None, 0, 10)   # not contiguous
+    d = np.empty(37, np.float32)
+    g.read_maps_noalloc(d, None, 100)           # the count follows the buffer
+    np.testing.assert_array_equal(d, g.read_maps()["depth"].ravel()[100:137])
