@@ -73,7 +73,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def parse():
+def parse(argv=None):
+    return parse_args(argv)
+
+
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -87,7 +91,7 @@ def parse():
     ap.add_argument("--texture-bilinear", action="store_true",
                     help="time the texture-filter precision form (AMH_FLAG_TEXTURE_BILINEAR) instead of the "
                          "default FP32-blend form")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_setup(want_cuda: bool):
@@ -106,6 +110,33 @@ def dist_setup(want_cuda: bool):
         dist.init_process_group("nccl" if want_cuda else "gloo", timeout=timeout)
         pg = dist
     return rank, world, local, pg
+
+
+def spawn_ranks(n: int, cmd: list[str], port: int | None = None) -> int:
+    """Launch `cmd` as n local ranks, one process per GPU (RANK = LOCAL_RANK =
+    r, WORLD_SIZE = n, rendezvous on 127.0.0.1), wait for all of them and
+    return the first non-zero exit code (0 when every rank succeeded)."""
+    import socket
+    if port is None:
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+    procs = []
+    for r in range(n):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(n), LOCAL_WORLD_SIZE=str(n),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen(cmd, env=env))
+    rcs = [p.wait() for p in procs]
+    return next((rc for rc in rcs if rc), 0)
+
+
+def check_world(gpus: int) -> str | None:
+    """None when the launcher's world size (WORLD_SIZE, 1 without one) is the
+    --gpus the run was asked for, else the reason it is not."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != gpus:
+        return f"--gpus {gpus} but the launcher started {world} rank(s)"
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -251,13 +282,75 @@ def workload_config(sc):
             "l2": "inputs larger than L2: ~280 MB resident per context (textures + state) vs 129 MB L2"}
 
 
-def run_ours(args):
+def run_ours(args, measure=None, scene=None, want_cuda: bool = True):
+    """This project's arm: every rank times its own reference view (device
+    work in `measure`, by default measure_device); the job's time is the
+    slowest rank's and rank 0 prints the JSON line.  `measure`, `scene` and
+    `want_cuda` exist for the multi-rank host test, which runs this on CPU
+    ranks with a stub in place of the device work."""
+    bad = check_world(args.gpus)
+    if bad:
+        print(f"bench.py: {bad}", file=sys.stderr)
+        return 2
+    rank, world, local, dist = dist_setup(want_cuda)
+    dev = "cuda" if want_cuda else "cpu"
+    pg = (dist.get_backend() if dist else "none")
+    print(f"bench rank {rank}: device {dev}:{local}, process group {pg}, world size {world}", file=sys.stderr,
+          flush=True)
+    if scene is None:
+        from paper_1805_07920_gb300 import synth
+        scene = synth.make_scene(SCENE)
+    sc = assign_reference(scene, rank)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    m = (measure or measure_device)(args, sc, rank, world, local, barrier)
+    ms = max_over_ranks(m["ms"], dist, dev)
+    value = job_rate(sc.width * sc.height, ITERS, args.steps, world, ms)
+    e2e = m.get("e2e")
+    if e2e is not None:
+        e_ms = max_over_ranks(e2e.pop("ms"), dist, dev)
+        e2e = {"value": round(job_rate(sc.width * sc.height, ITERS, e2e["steps"], world, e_ms), 3), "unit": UNIT,
+               **e2e}
+    refs = [sc.ref]
+    if dist:
+        refs = [None] * world
+        dist.all_gather_object(refs, sc.ref)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ray-cast scene)",
+            "config": workload_config(sc) | {"parallelism": f"replicas{world}: one reference view per GPU",
+                                             "interpolation": m.get("form", "fp32_blend"),
+                                             "reference_per_rank": refs},
+            "roofline": m.get("roofline"), "cpu_baseline": m.get("cpu_baseline"),
+            "cpu_baseline_all_cores": m.get("cpu_baseline_all_cores"), "e2e": e2e,
+            "extras": m.get("extras", {}),
+            "clocks": m.get("clocks"), "gpu_launches": m.get("gpu_launches"),
+            "pairs_per_step": m.get("pairs_per_step"),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_device(args, sc, rank, world, local, barrier):
+    """The device work of one rank: init + 6 iterations of its reference view
+    per step, timed with CUDA events on the launching stream after a barrier;
+    then the roofline of the phase kernel, the end-to-end run through the
+    C-ABI with host buffers, the other forms and the oracle on the host
+    (rank 0 of a one-rank job only)."""
     import torch
-    rank, world, local, dist = dist_setup(True)
     torch.cuda.set_device(local)
     from paper_1805_07920_gb300 import amh
     amh.lib()
-    sc = rank_scene(rank)
     W, H = sc.width, sc.height
     form_flags = amh.AMH_FLAG_TEXTURE_BILINEAR if args.texture_bilinear else 0
     form = "texture_bilinear" if args.texture_bilinear else "fp32_blend"
@@ -279,8 +372,7 @@ def run_ours(args):
     pairs_phase = ctx.pair_count(reset=True)
 
     clock = ClockSampler(local)
-    if dist:
-        dist.barrier()
+    barrier()
     torch.cuda.synchronize()
     clock.start()
     time.sleep(0.3)
@@ -304,10 +396,7 @@ def run_ours(args):
     clocks = clock.stop()
     ms = ev0.elapsed_time(ev1)
     phase_ms = float(np.mean([a.elapsed_time(b) for a, b in ph]))
-    ms = max_over_ranks(ms, dist, "cuda")
-    if dist:
-        dist.barrier()
-    value = job_rate(W * H, ITERS, args.steps, world, ms)
+    barrier()
 
     # roofline of the dominant kernel (the colour-phase kernel)
     props = torch.cuda.get_device_properties(local)
@@ -353,17 +442,14 @@ def run_ours(args):
                                     amh.AMH_MEM_HOST)
             c.close()
         e2e_step()
-        if dist:
-            dist.barrier()
+        barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1e3
-        e_ms = max_over_ranks(e_ms, dist, "cuda")
-        e2e = {"value": round(job_rate(W * H, ITERS, args.e2e_steps, world, e_ms), 3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+        e2e = {"ms": e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "amh_create from pinned host images + init + 6 iterations + amh_read_maps to pinned "
                        "host + amh_destroy"}
 
@@ -372,7 +458,7 @@ def run_ours(args):
         if not args.texture_bilinear:
             extras["texture_bilinear_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "texture")
             extras["images_f16_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "f16")
-        extras["batched_ring20"] = bench_batch(args, dist)
+        extras["batched_ring20"] = bench_batch(args, None)
         extras["learned_proposal_1600x1056"] = bench_learned()
 
     cpu = cpu_all = None
@@ -387,25 +473,9 @@ def run_ours(args):
         cpu_all = {"value": round(va, 6), "unit": UNIT, "cores": ncores, "kind": "oracle",
                    "sample": f"the same oracle with the rows of each phase split over {ncores} host threads: init + "
                              f"{ia['iterations']} iteration(s) on a {ia['crop']} centred crop ({ia['seconds']} s)"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded ray-cast scene)",
-            "config": workload_config(sc) | {"parallelism": f"replicas{world}: one reference view per GPU",
-                                             "interpolation": form},
-            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
-            "extras": extras,
-            "clocks": clocks, "gpu_launches": args.steps * (1 + 2 * ITERS),
-            "pairs_per_step": pairs_init + pairs_phase,
-        }
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    return 0
+    return {"ms": ms, "form": form, "roofline": roofline, "e2e": e2e, "extras": extras, "clocks": clocks,
+            "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+            "gpu_launches": args.steps * (1 + 2 * ITERS), "pairs_per_step": pairs_init + pairs_phase}
 
 
 def bench_form(sc, steps, default_phase_ms, default_ctx, form):
@@ -580,6 +650,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: one process per GPU, started here
+        return spawn_ranks(args.gpus, [sys.executable, os.path.abspath(__file__), *sys.argv[1:]])
     return run_ours(args)
 
 
