@@ -91,6 +91,9 @@ def parse_args(argv=None):
     ap.add_argument("--texture-bilinear", action="store_true",
                     help="time the texture-filter precision form (AMH_FLAG_TEXTURE_BILINEAR) instead of the "
                          "default FP32-blend form")
+    ap.add_argument("--staged-fetch", action="store_true",
+                    help="time the shared-memory staged matrix sweep (AMH_FLAG_STAGED_FETCH) instead of the "
+                         "default texture-only fetch path")
     return ap.parse_args(argv)
 
 
@@ -352,8 +355,11 @@ def measure_device(args, sc, rank, world, local, barrier):
     from paper_1805_07920_gb300 import amh
     amh.lib()
     W, H = sc.width, sc.height
-    form_flags = amh.AMH_FLAG_TEXTURE_BILINEAR if args.texture_bilinear else 0
+    form_flags = (amh.AMH_FLAG_TEXTURE_BILINEAR if args.texture_bilinear else 0) | \
+        (amh.AMH_FLAG_STAGED_FETCH if args.staged_fetch else 0)
     form = "texture_bilinear" if args.texture_bilinear else "fp32_blend"
+    if args.staged_fetch:
+        form += "+staged"
     ctx = amh.Context.from_scene(sc, seed=SEED, flags=form_flags)
     stream = torch.cuda.current_stream()
 
@@ -369,7 +375,7 @@ def measure_device(args, sc, rank, world, local, barrier):
     ctx.init_random()
     pairs_init = ctx.pair_count(reset=True)
     ctx.iterate(ITERS)
-    pairs_phase = ctx.pair_count(reset=True)
+    pairs_phase, staged_phase = ctx.pair_counts(reset=True)
 
     clock = ClockSampler(local)
     barrier()
@@ -415,9 +421,14 @@ def measure_device(args, sc, rank, world, local, barrier):
     # gather rate of this GPU measured in this run by a gather-only loop
     gpeak = amh.gather_peak()
     samples_per_s = pairs_phase / (2 * ITERS) * SAMPLES_PER_PAIR / (phase_ms * 1e-3)
-    roofline["fetch"] = {"bound": "texture gather", "achieved": round(samples_per_s / 1e12, 4),
+    tex_per_s = (pairs_phase - staged_phase) / (2 * ITERS) * SAMPLES_PER_PAIR / (phase_ms * 1e-3)
+    roofline["staged_pair_fraction"] = round(staged_phase / max(1, pairs_phase), 4)
+    roofline["fetch"] = {"bound": "texture gather", "achieved": round(tex_per_s / 1e12, 4),
                          "peak": round(gpeak / 1e12, 4), "unit": "T samples/s",
-                         "frac": round(samples_per_s / gpeak, 4),
+                         "frac": round(tex_per_s / gpeak, 4),
+                         "all_samples_per_s": round(samples_per_s / 1e12, 4),
+                         "note": "achieved counts the samples fetched through the texture unit; the staged "
+                                 "fraction of the evaluations reads shared-memory boxes instead",
                          "peak_basis": "amh_gather_peak: gather-only loop over update-like windows, measured live"}
 
     # end to end through the C-ABI with host buffers
@@ -455,7 +466,8 @@ def measure_device(args, sc, rank, world, local, barrier):
 
     extras = {}
     if not args.no_extras and world == 1:     # one-GPU measurements of the other forms
-        if not args.texture_bilinear:
+        if not args.texture_bilinear and not args.staged_fetch:
+            extras["staged_fetch_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "staged")
             extras["texture_bilinear_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "texture")
             extras["images_f16_3200x2112"] = bench_form(sc, args.steps, phase_ms, ctx, "f16")
         extras["batched_ring20"] = bench_batch(args, None)
@@ -479,16 +491,22 @@ def measure_device(args, sc, rank, world, local, barrier):
 
 
 def bench_form(sc, steps, default_phase_ms, default_ctx, form):
-    """The same workload in one of the precision forms -- "texture": the
-    texture unit's filter interpolates (AMH_FLAG_TEXTURE_BILINEAR); "f16": the
-    images stored as FP16 (AMH_FLAG_IMAGES_F16) -- : throughput, phase-launch
-    time, and the fraction of pixels within 1 % of the ground truth next to
-    the default form's (both after the last timed step)."""
+    """The same workload in another form -- "texture": the texture unit's
+    filter interpolates (AMH_FLAG_TEXTURE_BILINEAR); "f16": the images stored
+    as FP16 (AMH_FLAG_IMAGES_F16); "staged": the matrix sampled from
+    shared-memory boxes where the windows fit (AMH_FLAG_STAGED_FETCH) -- :
+    throughput, phase-launch time, and the fraction of pixels
+    within 1 % of the ground truth next to the default form's (both after the
+    last timed step)."""
     import torch
     from paper_1805_07920_gb300 import amh
     if form == "texture":
         ctx = amh.Context.from_scene(sc, seed=SEED, flags=amh.AMH_FLAG_TEXTURE_BILINEAR)
         what = "texture-unit linear filter (fractions and their product rounded to 1/256)"
+    elif form == "staged":
+        ctx = amh.Context.from_scene(sc, seed=SEED, flags=amh.AMH_FLAG_STAGED_FETCH)
+        what = ("the 8 x N matrix sampled from shared-memory boxes of bilinear cells where a warp's windows fit "
+                "(t >= 1), the rest through the texture unit")
     else:
         ctx = amh.Context.from_scene(sc, seed=SEED, images=[im.astype(np.float16) for im in sc.images])
         what = "images stored as FP16 textures, FP32 interpolation and moments"

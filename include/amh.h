@@ -84,7 +84,16 @@ enum {
    * FP32 blends of gathered texels (fewer instructions per sample).  uint8
    * images and the method's own propagation / view selection only (amh_create
    * and amh_batch_create reject other combinations). */
-  AMH_FLAG_TEXTURE_BILINEAR = 16
+  AMH_FLAG_TEXTURE_BILINEAR = 16,
+  /* Fetch path of the 8 x N matrix of Eq. (1) in single contexts (a
+   * measured alternative; the default fetches every window sample through
+   * the texture unit): from t = 1 on, per block of pixels and source view, a
+   * shared-memory box of 40 x 40 bilinear cells is filled from the texture
+   * and serves the samples of every warp whose windows of a (hypothesis,
+   * view) pair all fit inside; the other samples use the texture unit.  The
+   * interpolation is FP32 either way, in a different order of operations, so
+   * results agree with the default path to rounding, not bit for bit. */
+  AMH_FLAG_STAGED_FETCH = 32
 };
 
 typedef struct amh_ctx amh_ctx;
@@ -419,6 +428,10 @@ AMH_API int amh_get_info(const amh_ctx* ctx, int32_t* width, int32_t* height,
  * since the last reset (each is one 36-sample warped bilateral NCC).  The
  * count is kept on the device; reading it synchronises the stream. */
 AMH_API int amh_pair_count(amh_ctx* ctx, uint64_t* count, int32_t reset);
+/* The same count (total, may be NULL) and, of those, the evaluations whose 36
+ * samples were read from a shared-memory box instead of the texture unit
+ * (staged, may be NULL; see AMH_FLAG_STAGED_FETCH).  reset clears both. */
+AMH_API int amh_pair_counts(amh_ctx* ctx, uint64_t* total, uint64_t* staged, int32_t reset);
 
 /* Wait for all work of the context; reports kernel status errors. */
 AMH_API int amh_synchronize(amh_ctx* ctx);

@@ -22,12 +22,13 @@ AMH_FLAG_SYMMETRIC_PROPAGATION = 4   # ablation: symmetric checkerboard propagat
 AMH_FLAG_HEURISTIC_VIEWS = 8         # ablation: per-hypothesis k-best view selection
 AMH_FLAG_IMAGES_F16 = 2
 AMH_FLAG_TEXTURE_BILINEAR = 16       # precision form: texture-unit bilinear interpolation
+AMH_FLAG_STAGED_FETCH = 32           # fetch path: shared-memory staged matrix sweep (measured alternative)
 MAX_SRC = 32
 NOALLOC_MAX_PIXELS = 262144
 
 EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_random",
            "amh_step_phase", "amh_iterate", "amh_get_state", "amh_set_state", "amh_read_maps",
-           "amh_get_info", "amh_pair_count", "amh_synchronize", "amh_last_error", "amh_destroy",
+           "amh_get_info", "amh_pair_count", "amh_pair_counts", "amh_synchronize", "amh_last_error", "amh_destroy",
            "amh_read_maps_noalloc", "amh_batch_create", "amh_batch_init_random", "amh_batch_step_phase",
            "amh_batch_iterate", "amh_batch_run", "amh_batch_set_variant", "amh_batch_autotune",
            "amh_batch_info", "amh_batch_get_state", "amh_batch_pair_count", "amh_batch_synchronize",
@@ -89,6 +90,7 @@ def lib():
         L.amh_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                    ctypes.POINTER(_i32)]
         L.amh_pair_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _i32]
+        L.amh_pair_counts.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _i32]
         L.amh_synchronize.argtypes = [_vp]
         L.amh_last_error.argtypes = [_vp]
         L.amh_last_error.restype = ctypes.c_char_p
@@ -286,6 +288,13 @@ class Context:
         c = ctypes.c_uint64()
         self._check(lib().amh_pair_count(self.ctx, ctypes.byref(c), int(reset)))
         return c.value
+
+    def pair_counts(self, reset: bool = False) -> tuple[int, int]:
+        """(all evaluations, those sampled from shared-memory boxes) since the
+        last reset."""
+        c, st = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(lib().amh_pair_counts(self.ctx, ctypes.byref(c), ctypes.byref(st), int(reset)))
+        return c.value, st.value
 
     # ---- state ----
     def get_state(self):

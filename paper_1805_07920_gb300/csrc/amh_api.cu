@@ -239,8 +239,8 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   CTRY(dev_alloc((void**)&c->d_vbest, np));
   CTRY(dev_alloc((void**)&c->d_wmask, np * sizeof(uint32_t)));
   CTRY(dev_alloc((void**)&c->d_choice, np));
-  CTRY(dev_alloc((void**)&c->d_pairs, kPairCounters * sizeof(unsigned long long)));
-  CTRY(cudaMemsetAsync(c->d_pairs, 0, kPairCounters * sizeof(unsigned long long), c->stream));
+  CTRY(dev_alloc((void**)&c->d_pairs, 2 * kPairCounters * sizeof(unsigned long long)));
+  CTRY(cudaMemsetAsync(c->d_pairs, 0, 2 * kPairCounters * sizeof(unsigned long long), c->stream));
   CTRY(dev_alloc((void**)&c->d_status, sizeof(unsigned int)));
   CTRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
 
@@ -261,6 +261,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
   a.img_half = half ? 1 : 0;
   a.ablation = ((p->flags & AMH_FLAG_SYMMETRIC_PROPAGATION) ? 1 : 0) | ((p->flags & AMH_FLAG_HEURISTIC_VIEWS) ? 2 : 0);
   a.tex_filter = (p->flags & AMH_FLAG_TEXTURE_BILINEAR) ? 1 : 0;
+  a.staged = (p->flags & AMH_FLAG_STAGED_FETCH) ? 1 : 0;
   a.dmin = p->depth_min;
   a.dmax = p->depth_max;
   a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
@@ -282,7 +283,7 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     const int v = src[j];
     c->src[j] = v;
     const amh_camera& cj = cams[v];
-    // relative pose ref -> j, then A = K_j R_jr K_ref^-1, b = K_j t_jr
+    // relative pose ref -> j, then P = K_j R_jr, A = P K_ref^-1, b = K_j t_jr
     double Rjr[9], tjr[3], A[9], KR[9], b[3];
     mul3(cj.R, RrT, Rjr);
     for (int i = 0; i < 3; i++)
@@ -291,11 +292,15 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
     mul3(KR, Kri, A);
     for (int i = 0; i < 3; i++) b[i] = cj.K[3 * i] * tjr[0] + cj.K[3 * i + 1] * tjr[1] + cj.K[3 * i + 2] * tjr[2];
     // shift the output by (+1, +1): rows 0 and 1 gain row 2
-    for (int q = 0; q < 3; q++) { A[q] += A[6 + q]; A[3 + q] += A[6 + q]; }
+    for (int q = 0; q < 3; q++) {
+      A[q] += A[6 + q]; A[3 + q] += A[6 + q];
+      KR[q] += KR[6 + q]; KR[3 + q] += KR[6 + q];
+    }
     b[0] += b[2];
     b[1] += b[2];
     ViewConst& V = a.v[j];
     for (int i = 0; i < 9; i++) V.A[i] = (float)A[i];
+    for (int i = 0; i < 9; i++) V.P[i] = (float)KR[i];
     for (int i = 0; i < 3; i++) V.b[i] = (float)b[i];
     V.xmax = (float)cj.width;
     V.ymax = (float)cj.height;
@@ -518,16 +523,24 @@ AMH_API int amh_get_info(const amh_ctx* c, int32_t* w, int32_t* h, int32_t* n, i
   return AMH_OK;
 }
 
-AMH_API int amh_pair_count(amh_ctx* c, uint64_t* count, int32_t reset) {
+AMH_API int amh_pair_counts(amh_ctx* c, uint64_t* total, uint64_t* staged, int32_t reset) {
   if (!c) return AMH_EINVAL;
-  unsigned long long v[kPairCounters];
+  unsigned long long v[2 * kPairCounters];
   CUDA_TRY(c, cudaMemcpyAsync(v, c->d_pairs, sizeof v, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  unsigned long long tot = 0;
-  for (int i = 0; i < kPairCounters; i++) tot += v[i];
-  if (count) *count = tot;
+  unsigned long long tot = 0, st = 0;
+  for (int i = 0; i < kPairCounters; i++) {
+    tot += v[i];
+    st += v[kPairCounters + i];
+  }
+  if (total) *total = tot;
+  if (staged) *staged = st;
   if (reset) CUDA_TRY(c, cudaMemsetAsync(c->d_pairs, 0, sizeof v, c->stream));
   return AMH_OK;
+}
+
+AMH_API int amh_pair_count(amh_ctx* c, uint64_t* count, int32_t reset) {
+  return amh_pair_counts(c, count, nullptr, reset);
 }
 
 AMH_API int amh_synchronize(amh_ctx* c) {

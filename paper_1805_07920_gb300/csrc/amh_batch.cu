@@ -30,6 +30,8 @@ using namespace upd;
 
 constexpr int kBThreads = 128;
 constexpr int kMaxRefs = 256;
+constexpr int kViewWords = (int)(sizeof(ViewConst) / sizeof(float));   // a view table entry in 4-byte words
+static_assert(sizeof(ViewConst) % sizeof(float) == 0, "view table entries are whole words");
 
 // the fields update_pixel reads, for one reference of the batch
 struct RefArgs {
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_
       for (int i = threadIdx.x; i < words; i += blockDim.x)
         reinterpret_cast<int*>(&ra)[i] = reinterpret_cast<const int*>(&b.refs[r])[i];
       __syncthreads();
-      for (int i = threadIdx.x; i < ra.N * 16; i += blockDim.x)
+      for (int i = threadIdx.x; i < ra.N * kViewWords; i += blockDim.x)
         reinterpret_cast<float*>(ra.v)[i] = reinterpret_cast<const float*>(ra.vt)[i];
       if (threadIdx.x == 0) {
         ra.t = b.t;
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kBThreads) batch_init_kernel(const __grid_cons
       for (int i = threadIdx.x; i < words; i += blockDim.x)
         reinterpret_cast<int*>(&ra)[i] = reinterpret_cast<const int*>(&b.refs[r])[i];
       __syncthreads();
-      for (int i = threadIdx.x; i < ra.N * 16; i += blockDim.x)
+      for (int i = threadIdx.x; i < ra.N * kViewWords; i += blockDim.x)
         reinterpret_cast<float*>(ra.v)[i] = reinterpret_cast<const float*>(ra.vt)[i];
       if (threadIdx.x == 0) cur_ref = r;
       __syncthreads();
@@ -471,12 +473,16 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
       bmul3(cj.K, Rjr, KR);
       bmul3(KR, Kri, A);
       for (int i = 0; i < 3; i++) bb[i] = cj.K[3 * i] * tjr[0] + cj.K[3 * i + 1] * tjr[1] + cj.K[3 * i + 2] * tjr[2];
-      for (int q = 0; q < 3; q++) { A[q] += A[6 + q]; A[3 + q] += A[6 + q]; }
+      for (int q = 0; q < 3; q++) {
+        A[q] += A[6 + q]; A[3 + q] += A[6 + q];
+        KR[q] += KR[6 + q]; KR[3 + q] += KR[6 + q];
+      }
       bb[0] += bb[2];
       bb[1] += bb[2];
       ViewConst V;
       std::memset(&V, 0, sizeof V);
       for (int i = 0; i < 9; i++) V.A[i] = (float)A[i];
+      for (int i = 0; i < 9; i++) V.P[i] = (float)KR[i];
       for (int i = 0; i < 3; i++) V.b[i] = (float)bb[i];
       V.xmax = (float)cj.width;
       V.ymax = (float)cj.height;

@@ -23,17 +23,22 @@ constexpr int kPairCounters = 64;        // striped evaluation counters
 
 // One source view.  A and b give the homography of a plane (n, d) as
 // H = A - b c^T with c = K_ref^-T n / d (Sec. 2: planes in scene space), where
-// A = K_j R_jr K_ref^-1 and b = K_j t_jr; rows 0 and 1 already hold row 2
-// added once, so H maps reference pixels to source coordinates + (1, 1): with
-// integer part f of such a coordinate, tex2Dgather at f fetches the texels
-// (f - 1, f) = (floor(x), floor(x) + 1).
+// A = K_j R_jr K_ref^-1 and b = K_j t_jr; P = K_j R_jr.  Rows 0 and 1 of A, b
+// and P already hold row 2 added once, so H maps reference pixels to source
+// coordinates + (1, 1): with integer part f of such a coordinate, tex2Dgather
+// at f fetches the texels (f - 1, f) = (floor(x), floor(x) + 1).
+// The image of a window centre is taken from the plane's 3-D point there,
+// H (x, y, 1) = P ray + b / D (ray = K_ref^-1 (x, y, 1), D its depth), which
+// in FP32 stays accurate for planes seen nearly edge-on, where the terms of
+// H (x, y, 1) nearly cancel; the window offsets use H's first two columns.
 struct ViewConst {
   float A[9];
   float b[3];
+  float P[9];
   float xmax, ymax;          // width, height: valid shifted centres in [1, W] x [1, H]
   cudaTextureObject_t tex;   // point sampling, clamp; uint8 read as value / 255, or FP16
 };
-static_assert(sizeof(ViewConst) == 64, "ViewConst is 64 bytes");
+static_assert(sizeof(ViewConst) == 104, "ViewConst is 104 bytes");
 
 struct PhaseArgs {
   int W, H, N, color, t;
@@ -47,6 +52,7 @@ struct PhaseArgs {
   int img_half;              // images are FP16 (else uint8)
   int ablation;              // bit 0: symmetric propagation, bit 1: heuristic views (Sec. 4)
   int tex_filter;            // samples through the texture unit's linear filter
+  int staged;                // shared-memory staged matrix sweep (AMH_FLAG_STAGED_FETCH)
   float dmin, dmax;
   uint32_t key0, key1;       // Philox key (seed)
   const void* ref;           // reference image, W x H (uint8 or FP16)
@@ -174,15 +180,16 @@ __device__ __forceinline__ float3 normal_from_uniforms(float u1, float u2) {
 }
 
 // The cost needs c = K_ref^-T n / d (Sec. 2) with d = -D (n . ray) the plane
-// offset; the plane is usable when it faces the pixel (d > 0) at D > 0.
-__device__ __forceinline__ bool plane_c(const float* Ki, float4 pl, float3 ray, float3* c) {
+// offset, and 1 / D (the window centre's image, see ViewConst); the plane is
+// usable when it faces the pixel (d > 0) at D > 0.  c.w = 1 / D.
+__device__ __forceinline__ bool plane_c(const float* Ki, float4 pl, float3 ray, float4* c) {
   const float3 n = make_float3(pl.x, pl.y, pl.z);
   const float d = -pl.w * dot3(n, ray);
   const bool ok = (pl.w > 0.f) && (d > 0.f) && isfinite(d);
   const float id = ok ? 1.f / d : 0.f;
-  *c = make_float3((Ki[0] * n.x + Ki[3] * n.y + Ki[6] * n.z) * id,
+  *c = make_float4((Ki[0] * n.x + Ki[3] * n.y + Ki[6] * n.z) * id,
                    (Ki[1] * n.x + Ki[4] * n.y + Ki[7] * n.z) * id,
-                   (Ki[2] * n.x + Ki[5] * n.y + Ki[8] * n.z) * id);
+                   (Ki[2] * n.x + Ki[5] * n.y + Ki[8] * n.z) * id, ok ? 1.f / pl.w : 0.f);
   return ok;
 }
 

@@ -3,6 +3,7 @@
 // update itself is in amh_update.cuh).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "amh_device.cuh"
@@ -17,21 +18,38 @@ constexpr int kTile = 16;
 constexpr int kThreads = 128;
 constexpr int kPhaseBlocksPerSM = 3;          // 168 registers per thread
 
+// npairs: evaluations of this thread, plus 2^16 for each one sampled from a
+// shared-memory box (fewer than 2^11 per thread and launch); the two totals
+// go to the first and the second kPairCounters counters
 __device__ __forceinline__ void count_pairs(const PhaseArgs& a, int npairs) {
-  const int tot = __reduce_add_sync(0xffffffffu, npairs);
-  if ((threadIdx.x & 31) == 0 && tot)
-    atomicAdd(&a.pairs[(blockIdx.x * 4 + (threadIdx.x >> 5) + blockIdx.y * 7) % kPairCounters],
-              (unsigned long long)tot);
+  const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)npairs & 0xFFFFu);
+  const unsigned hi = __reduce_add_sync(0xffffffffu, (unsigned)npairs >> 16);
+  const int k = (blockIdx.x * 4 + (threadIdx.x >> 5) + blockIdx.y * 7) % kPairCounters;
+  if ((threadIdx.x & 31) == 0 && lo) atomicAdd(&a.pairs[k], (unsigned long long)lo);
+  if ((threadIdx.x & 31) == 0 && hi) atomicAdd(&a.pairs[kPairCounters + k], (unsigned long long)hi);
 }
 
 template <bool kHalf, int kMode>
 __global__ void __launch_bounds__(kThreads, kPhaseBlocksPerSM) phase_kernel(const __grid_constant__ PhaseArgs a) {
   PixelArrays sm;
   const int tid = threadIdx.x;
-  const int y = blockIdx.y * kTile + (tid >> 3);
-  const int x = blockIdx.x * kTile + 2 * (tid & 7) + ((y + a.color) & 1);
   int npairs = 0;
-  if (x < a.W && y < a.H) update_pixel<kHalf, kMode>(a, sm, x, y, &npairs);
+  if constexpr ((kMode & kStage) != 0) {
+    // Warp w updates rows 4w .. 4w + 3 of the tile (8 pixels of the colour
+    // per row); each quarter-warp takes 4 pixels of two neighbouring rows, so
+    // the 8 lanes of a 16-byte shared load sample 8 distinct columns modulo
+    // 8 of the box where the view maps the tile at unit scale.
+    const int lane = tid & 31, q = lane >> 3;
+    const int y = blockIdx.y * kTile + 4 * (tid >> 5) + 2 * (q >> 1) + ((lane >> 2) & 1);
+    const int x = blockIdx.x * kTile + 2 * (4 * (q & 1) + (lane & 3)) + ((y + a.color) & 1);
+    // the whole block takes part in the staged sweep, pixels outside the image too
+    __shared__ StageShared ss;
+    update_pixel<kHalf, kMode>(a, sm, x, y, &npairs, &ss, x < a.W && y < a.H);
+  } else {
+    const int y = blockIdx.y * kTile + (tid >> 3);
+    const int x = blockIdx.x * kTile + 2 * (tid & 7) + ((y + a.color) & 1);
+    if (x < a.W && y < a.H) update_pixel<kHalf, kMode>(a, sm, x, y, &npairs);
+  }
   count_pairs(a, npairs);
 }
 
@@ -78,13 +96,33 @@ int launch_init(const PhaseArgs& a, cudaStream_t s) {
 template <bool kHalf, int kMode>
 int launch_phase_t(const PhaseArgs& a, cudaStream_t s) {
   static std::once_flag once[64];
-  prefer_l1(phase_kernel<kHalf, kMode>, once);
+  if ((kMode & kStage) == 0) {
+    prefer_l1(phase_kernel<kHalf, kMode>, once);
+  } else {
+    // the smallest carve-out that holds the staged blocks' shared memory: the
+    // rest of the unified L1 stays texture and local-memory cache
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::call_once(once[dev & 63], [] {
+      int d = 0, smem_sm = 0;
+      cudaGetDevice(&d);
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+      const int need = kPhaseBlocksPerSM * (int)(sizeof(StageShared) + 1024);
+      const int pct = smem_sm > 0 ? std::min(100, (100 * need + smem_sm - 1) / smem_sm) : 100;
+      cudaFuncSetAttribute(phase_kernel<kHalf, kMode>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    });
+  }
   dim3 grid((a.W + kTile - 1) / kTile, (a.H + kTile - 1) / kTile);
   phase_kernel<kHalf, kMode><<<grid, kThreads, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
 template <int kMode>
 int launch_phase_m(const PhaseArgs& a, cudaStream_t s) {
+  // staged sweep on request; at t = 0 the planes are the random ones of the
+  // initialisation and no window set fits a box, so those phases fetch
+  // through the texture unit
+  if (a.staged && a.t > 0)
+    return a.img_half ? launch_phase_t<true, kMode | kStage>(a, s) : launch_phase_t<false, kMode | kStage>(a, s);
   return a.img_half ? launch_phase_t<true, kMode>(a, s) : launch_phase_t<false, kMode>(a, s);
 }
 // the method, or one of the ablations of Sec. 4 (a.ablation: bit 0 symmetric

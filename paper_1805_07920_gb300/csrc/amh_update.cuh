@@ -126,23 +126,106 @@ __device__ __forceinline__ void load_ref_window(const A& a, int x, int y, RefWin
 // (homogeneous depth <= 0 at a window corner; it is affine over the window),
 // projects the centre outside view j, or when a patch has no variance;
 // otherwise clamped to [0, 2].  Window samples outside the view are clamped to
-// its edge by the texture unit.
+// its edge by the texture unit (or, in a shared-memory box, by the gathers
+// that filled it).
 // ---------------------------------------------------------------------------
-template <bool kHalf, bool kTex = false>
-__device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok, float x, float y,
-                                          const RefWin& rw, int* evaluated) {
-  if (!ok) return kWorst;
-  const float H0 = fmaf(-V.b[0], c.x, V.A[0]), H1 = fmaf(-V.b[0], c.y, V.A[1]), H2 = fmaf(-V.b[0], c.z, V.A[2]);
-  const float H3 = fmaf(-V.b[1], c.x, V.A[3]), H4 = fmaf(-V.b[1], c.y, V.A[4]), H5 = fmaf(-V.b[1], c.z, V.A[5]);
-  const float H6 = fmaf(-V.b[2], c.x, V.A[6]), H7 = fmaf(-V.b[2], c.y, V.A[7]), H8 = fmaf(-V.b[2], c.z, V.A[8]);
-  const float pz = fmaf(H6, x, fmaf(H7, y, H8));
+
+// The homography of one (hypothesis, view) pair at one pixel: its linear part
+// (output shifted by (+1, +1), see ViewConst), the window centre's image
+// (px, py, pz) and (cx, cy), and the smallest homogeneous depth over the
+// window.
+struct PairGeom {
+  float H0, H1, H3, H4, H6, H7;
+  float px, py, pz, cx, cy, zmin;
+};
+
+// false: the pair costs 2 (behind the view over the window, or the centre
+// outside the view).  c = (K_ref^-T n / d, 1 / D), ray = K_ref^-1 (x, y, 1).
+__device__ __forceinline__ bool pair_geometry(const ViewConst& V, float4 c, float3 ray, PairGeom& G) {
+  const float H0 = fmaf(-V.b[0], c.x, V.A[0]), H1 = fmaf(-V.b[0], c.y, V.A[1]);
+  const float H3 = fmaf(-V.b[1], c.x, V.A[3]), H4 = fmaf(-V.b[1], c.y, V.A[4]);
+  const float H6 = fmaf(-V.b[2], c.x, V.A[6]), H7 = fmaf(-V.b[2], c.y, V.A[7]);
+  // H (x, y, 1) = P ray + b / D: the window centre's 3-D point projected
+  const float pz = fmaf(V.P[6], ray.x, fmaf(V.P[7], ray.y, fmaf(V.P[8], ray.z, V.b[2] * c.w)));
   const float zmin = pz - (float)kWinR * (fabsf(H6) + fabsf(H7));
-  if (!(zmin > 0.f)) return kWorst;
-  const float px = fmaf(H0, x, fmaf(H1, y, H2)), py = fmaf(H3, x, fmaf(H4, y, H5));
+  if (!(zmin > 0.f)) return false;
+  const float px = fmaf(V.P[0], ray.x, fmaf(V.P[1], ray.y, fmaf(V.P[2], ray.z, V.b[0] * c.w)));
+  const float py = fmaf(V.P[3], ray.x, fmaf(V.P[4], ray.y, fmaf(V.P[5], ray.z, V.b[1] * c.w)));
   const float iz = rcp_approx(pz);
   const float cx = px * iz, cy = py * iz;
-  if (!(cx >= 1.f && cx <= V.xmax && cy >= 1.f && cy <= V.ymax)) return kWorst;
-  *evaluated += 1;
+  if (!(cx >= 1.f && cx <= V.xmax && cy >= 1.f && cy <= V.ymax)) return false;
+  G.H0 = H0; G.H1 = H1; G.H3 = H3; G.H4 = H4; G.H6 = H6; G.H7 = H7;
+  G.px = px; G.py = py; G.pz = pz; G.cx = cx; G.cy = cy; G.zmin = zmin;
+  return true;
+}
+
+// Where the 36 window samples fetch their 2 x 2 texels: the texture unit's
+// gather (kFetchGather), its linear filter (kFetchFilter, the
+// AMH_FLAG_TEXTURE_BILINEAR form), or a shared-memory box of bilinear cells
+// built from the same gathers (kFetchBox).
+constexpr int kFetchGather = 0, kFetchFilter = 1, kFetchBox = 2;
+
+// Shared-memory sample box: kBoxW x kBoxH bilinear cells of one source view.
+// Cell (c, r) covers the texels (ox + c .. ox + c + 1, oy + r .. oy + r + 1)
+// and holds the coefficients of their bilinear interpolant,
+// (a, b, c', d) = (T00, T10 - T00, T01 - T00, T11 - T01 - T10 + T00), so that
+// a sample at fractions (fx, fy) inside the cell is a + fx b + fy (c' + fx d):
+// one 16-byte load and three FMAs.
+constexpr int kBoxW = 40, kBoxH = 40;
+struct SampleBox {
+  float4 q[kBoxH * kBoxW];
+};
+// Placement of one view's box for a block: its texel origin and the range
+// the (shifted) sample positions must stay in, with a quarter-texel margin
+// for rounding: floor(p) - 1 - ox in [0, kBoxW - 1], floor(p) - 1 - oy in
+// [0, kBoxH - 1].
+struct BoxPlace {
+  int ox, oy;
+  float bx0, bx1, by0, by1;
+};
+__device__ __forceinline__ BoxPlace make_place(int ox, int oy) {
+  BoxPlace b;
+  b.ox = ox;
+  b.oy = oy;
+  b.bx0 = (float)ox + 1.25f;
+  b.bx1 = (float)(ox + kBoxW) + 0.75f;
+  b.by0 = (float)oy + 1.25f;
+  b.by1 = (float)(oy + kBoxH) + 0.75f;
+  return b;
+}
+// Every sample of the window lies in the box: |x(u, v) - cx| <= 5 (|H0 - cx
+// H6| + |H1 - cx H7|) / zmin over the window offsets u, v in [-5, 5] (the
+// numerator of x - cx is linear in (u, v), the denominator at least zmin), and
+// likewise for y.
+__device__ __forceinline__ bool window_in_box(const PairGeom& G, const BoxPlace& b) {
+  const float izm = rcp_approx(G.zmin);
+  const float R = (float)kWinR;
+  const float ex = R * (fabsf(fmaf(-G.cx, G.H6, G.H0)) + fabsf(fmaf(-G.cx, G.H7, G.H1))) * izm;
+  const float ey = R * (fabsf(fmaf(-G.cy, G.H6, G.H3)) + fabsf(fmaf(-G.cy, G.H7, G.H4))) * izm;
+  return G.cx - ex >= b.bx0 && G.cx + ex <= b.bx1 && G.cy - ey >= b.by0 && G.cy + ey <= b.by1;
+}
+// floor of both lanes (as floor2) and the integer parts as the bits of
+// x + 2^23 rounded towards -inf: 0x4B000000 + floor(x) for 0 <= x < 2^23
+__device__ __forceinline__ f2 floor2_bits(f2 x, uint32_t& bx, uint32_t& by) {
+  const f2 M = pack2(8388608.f, 8388608.f);
+  f2 t;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(t.v) : "l"(x.v), "l"(M.v));
+  float tx, ty;
+  unpack2(t, tx, ty);
+  bx = __float_as_uint(tx);
+  by = __float_as_uint(ty);
+  return sub2(t, M);
+}
+
+// The 36 samples of one pair and the NCC of Eq. (8).  kFetchBox: box_cells
+// is the box's cell array and box_adj its box_adjust(), so that the cell of
+// a sample whose floored positions have the bits (bx, by) is
+// by kBoxW + bx - box_adj.
+template <bool kHalf, int kFetch>
+__device__ __forceinline__ float ncc_window(const ViewConst& V, const PairGeom& G, const RefWin& rw,
+                                            const void* box_cells = nullptr, uint32_t box_adj = 0u) {
+  const float H0 = G.H0, H1 = G.H1, H3 = G.H3, H4 = G.H4, H6 = G.H6, H7 = G.H7;
+  const float px = G.px, py = G.py, pz = G.pz;
   const float R = (float)kWinR, St = (float)kWinStride;
   const float sx0 = fmaf(-R, H0 + H1, px), sy0 = fmaf(-R, H3 + H4, py), sz0 = fmaf(-R, H6 + H7, pz);
   const float cxs = St * H0, cys = St * H3, czs = St * H6;
@@ -150,7 +233,9 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
   // Packed f32x2 arithmetic: the (x, y) position, floor and fraction of each
   // sample form one lane pair (the gather takes them as a pair), the depths
   // and the three moments of samples (cb, cb + 1) of a row another; the
-  // gathers and the bilinear blends are per sample.
+  // fetches and the bilinear blends are per sample.
+  const float4* box = reinterpret_cast<const float4*>(box_cells);
+  if (kFetch == kFetchBox) __builtin_assume(__isShared(box) != 0);
   const f2 cxy = pack2(cxs, cys), cz2 = pack2(czs, czs);
   f2 acc1 = pack2(0.f, 0.f), acc2 = pack2(0.f, 0.f), accr = pack2(0.f, 0.f);
   f2 s0p = pack2(0.f, 0.f);
@@ -172,7 +257,7 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
       const float ia = rcp_approx(qz0), ib = rcp_approx(qz1);
       const f2 pa = pack2(qxa * ia, qya * ia), pb = pack2(qxb * ib, qyb * ib);
       f2 sp;
-      if (kTex) {
+      if (kFetch == kFetchFilter) {
         // the texture unit's linear filter (AMH_FLAG_TEXTURE_BILINEAR): its
         // texel centres sit at +0.5, the positions here at +1
         const f2 ha = sub2(pa, pack2(0.5f, 0.5f)), hb = sub2(pb, pack2(0.5f, 0.5f));
@@ -180,6 +265,19 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
         unpack2(ha, hxa, hya);
         unpack2(hb, hxb, hyb);
         sp = pack2(tex2D<float>(V.tex, hxa, hya), tex2D<float>(V.tex, hxb, hyb));
+      } else if (kFetch == kFetchBox) {
+        // cell index (floor(p) - 1 - o) from the bits of the floored
+        // positions; box_adj folds in the origin and the 2^23 offsets
+        uint32_t bxa, bya, bxb, byb;
+        const f2 fla = floor2_bits(pa, bxa, bya), flb = floor2_bits(pb, bxb, byb);
+        const f2 fra = sub2(pa, fla), frb = sub2(pb, flb);
+        const float4 ca = box[bya * (uint32_t)kBoxW + bxa - box_adj];
+        const float4 cb4 = box[byb * (uint32_t)kBoxW + bxb - box_adj];
+        float fxa, fya, fxb, fyb;
+        unpack2(fra, fxa, fya);
+        unpack2(frb, fxb, fyb);
+        sp = pack2(fmaf(fya, fmaf(fxa, ca.w, ca.z), fmaf(fxa, ca.y, ca.x)),
+                   fmaf(fyb, fmaf(fxb, cb4.w, cb4.z), fmaf(fxb, cb4.y, cb4.x)));
       } else {
         const f2 fla = floor2(pa), flb = floor2(pb);
         const f2 fra = sub2(pa, fla), frb = sub2(pb, flb);
@@ -224,6 +322,110 @@ __device__ __forceinline__ float ncc_cost(const ViewConst& V, float3 c, bool ok,
   return fminf(fmaxf(1.f - cov * (S * rsqrtf(vv)), 0.f), 2.f);
 }
 
+template <bool kHalf, bool kTex = false>
+__device__ __forceinline__ float ncc_cost(const ViewConst& V, float4 c, bool ok, float3 ray,
+                                          const RefWin& rw, int* evaluated) {
+  if (!ok) return kWorst;
+  PairGeom G;
+  if (!pair_geometry(V, c, ray, G)) return kWorst;
+  *evaluated += 1;
+  return ncc_window<kHalf, kTex ? kFetchFilter : kFetchGather>(V, G, rw);
+}
+
+// The same cost inside the staged matrix sweep, where the whole warp calls
+// it together: when every lane that evaluates the pair has its window inside
+// the block's box of this view, the warp samples the box, otherwise the
+// texture unit (the two interpolate the same texels in FP32, in a different
+// order of operations).
+template <bool kHalf>
+__device__ __forceinline__ float ncc_cost_boxed(const ViewConst& V, float4 c, bool ok, float3 ray,
+                                                const RefWin& rw, int* evaluated, const BoxPlace& bp,
+                                                const SampleBox& box, uint32_t box_adj) {
+  PairGeom G;
+  const bool act = ok && pair_geometry(V, c, ray, G);
+  const bool fits = act && window_in_box(G, bp);
+  const bool all_fit = __all_sync(0xffffffffu, fits || !act);
+  float m = kWorst;
+  if (act) {
+    *evaluated += all_fit ? 0x10001 : 1;      // the high half counts box-sampled evaluations
+    m = all_fit ? ncc_window<kHalf, kFetchBox>(V, G, rw, box.q, box_adj) : ncc_window<kHalf, kFetchGather>(V, G, rw);
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Staged matrix sweep: per block and source view, one shared-memory box of
+// texel pairs around where the block's pixels' own planes put their windows;
+// every warp whose windows of a (hypothesis, view) pair all lie in it samples
+// the box instead of the texture unit.
+// ---------------------------------------------------------------------------
+constexpr int kStageWarps = 8;          // blocks of up to 256 threads
+constexpr int kStageLane = 12;          // the lane whose own plane places its warp's candidate
+struct StageShared {
+  SampleBox box;
+  BoxPlace place[kMaxSrc];
+  float2 wcen[kStageWarps][kMaxSrc];    // per warp and view: window centre of lane kStageLane, NaN if none
+};
+
+// Box origins of every view for this block (block-wide; ends synchronised):
+// each warp proposes the window centre its lane kStageLane's own plane
+// projects to; the box is centred on the median of the proposals.
+template <class A>
+__device__ __forceinline__ void place_boxes(const A& a, StageShared& ss, float4 c_own, bool own_ok, float3 ray) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == kStageLane) {
+    for (int j = 0; j < a.N; j++) {
+      PairGeom G;
+      const bool ok = own_ok && pair_geometry(a.v[j], c_own, ray, G);
+      ss.wcen[warp][j] = ok ? make_float2(G.cx, G.cy) : make_float2(__int_as_float(0x7fc00000), 0.f);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < a.N; j += blockDim.x) {
+    float xs[kStageWarps], ys[kStageWarps];
+    int n = 0;
+    for (int w = 0; w < nw; w++) {
+      const float2 m = ss.wcen[w][j];
+      if (m.x == m.x) {                     // insertion into the sorted lists
+        int i = n++;
+        while (i > 0 && xs[i - 1] > m.x) { xs[i] = xs[i - 1]; i--; }
+        xs[i] = m.x;
+        i = n - 1;
+        while (i > 0 && ys[i - 1] > m.y) { ys[i] = ys[i - 1]; i--; }
+        ys[i] = m.y;
+      }
+    }
+    int ox = -1, oy = -1;
+    if (n > 0) {
+      // (shifted) centre c sits on real texel c - 1 at the middle of the box
+      const float cx = 0.5f * (xs[(n - 1) >> 1] + xs[n >> 1]), cy = 0.5f * (ys[(n - 1) >> 1] + ys[n >> 1]);
+      ox = max(-1, (int)floorf(cx - 1.f - 0.5f * (float)(kBoxW - 1)));
+      oy = max(-1, (int)floorf(cy - 1.f - 0.5f * (float)(kBoxH - 1)));
+    }
+    ss.place[j] = make_place(ox, oy);
+  }
+  __syncthreads();
+}
+
+// The box of view V at bp: one gather per cell (its four texels; the texture
+// unit clamps coordinates outside the view, exactly as for the samples it
+// serves directly), turned into the cell's coefficients.
+__device__ __forceinline__ void fill_box(const ViewConst& V, SampleBox& B, const BoxPlace& bp) {
+  for (int i = threadIdx.x; i < kBoxH * kBoxW; i += blockDim.x) {
+    const int r = i / kBoxW, cc = i - r * kBoxW;
+    const float4 g = tex2Dgather<float4>(V.tex, (float)(bp.ox + cc + 1), (float)(bp.oy + r + 1), 0);
+    const float b = g.z - g.w;
+    B.q[i] = make_float4(g.w, b, g.x - g.w, (g.y - g.x) - b);
+  }
+}
+
+// Cell index of the sample whose floored positions have the bits (bx, by):
+// by kBoxW + bx - box_adjust(bp)  (mod 2^32)
+__device__ __forceinline__ uint32_t box_adjust(const BoxPlace& bp) {
+  const uint32_t K = 0x4B000000u;
+  return (K + 1u + (uint32_t)bp.oy) * (uint32_t)kBoxW + K + 1u + (uint32_t)bp.ox;
+}
+
 // Refinement candidate idx (Sec. 3.3): rho_t = 2^-(t+1); 0: depth and normal
 // perturbed (bisection); from t = 3 on also 1: (random D, n), 2: (D, random
 // n), 3: (random D, random n), 4: (perturbed D, n), 5: (D, perturbed n).
@@ -262,15 +464,15 @@ __device__ __forceinline__ float4 refine_candidate(const A& a, int x, int y, flo
 
 // Per-pixel working arrays of one thread (local memory, cached in L1): the
 // 8 x N cost matrix of Eq. (1), the N view weights and the 8 propagated planes
-// as c = K^-T n / d.  Shared memory stays unused so that L1 serves the texture
+// as (c = K^-T n / d, 1 / D).  Shared memory stays unused so that L1 serves the texture
 // gathers.
 struct PixelArrays {
   float M[kRegions * kMaxSrc];
   float w[kMaxSrc];
-  float C[kRegions * 3];
+  float4 C[kRegions];
   __device__ float& m(int g, int j, int) { return M[g * kMaxSrc + j]; }
   __device__ float& wt(int j) { return w[j]; }
-  __device__ float& cc(int g, int e) { return C[g * 3 + e]; }
+  __device__ float4& cc(int g) { return C[g]; }
 };
 
 // Eqs. (2)-(6): weights of the N views from the 8 x N matrix (rows of invalid
@@ -375,21 +577,29 @@ constexpr int kSymmetric = 1, kHeuristic = 2;
 // kTexture: window samples through the texture unit's linear filter
 // (AMH_FLAG_TEXTURE_BILINEAR) instead of gathers and FP32 blends.
 constexpr int kTexture = 4;
+// kStage: the 8 x N matrix sweep stages shared-memory sample boxes (the whole
+// block calls update_pixel together, pixels outside the image included)
+constexpr int kStage = 8;
 
 // ---------------------------------------------------------------------------
 // one pixel's checkerboard update
 // ---------------------------------------------------------------------------
 template <bool kHalf, int kMode = 0, class A>
 __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x, int y,
-                                             int* npairs) {
+                                             int* npairs, StageShared* ss = nullptr, bool live = true) {
   constexpr bool kTex = (kMode & kTexture) != 0;
+  constexpr bool kStaged = (kMode & kStage) != 0;
+  static_assert(!(kStaged && kTex), "the staged sweep gathers; the texture-filter form does not stage");
   const int N = a.N;
-  const size_t pi = checked_index(a, (size_t)y * a.W + x, (size_t)a.W * a.H, kBadPixel);
+  const size_t pi = live ? checked_index(a, (size_t)y * a.W + x, (size_t)a.W * a.H, kBadPixel) : 0;
   const float fx = (float)x, fy = (float)y;
   const float3 ray = ref_ray(a.Kinv, fx, fy);
 
   // --- Sec. 3.1: asymmetric checkerboard propagation ---------------------------
   int pick[kRegions];
+#pragma unroll
+  for (int g = 0; g < kRegions; g++) pick[g] = -1;
+  if (live) {
 #pragma unroll
   for (int g = 0; g < kRegions; g++) {
     int best = -1;
@@ -411,6 +621,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     }
     pick[g] = best;
   }
+  }
   float hD[kRegions];
   uint32_t valid = 0;
 #pragma unroll
@@ -426,36 +637,58 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     if (!(den < 0.f)) continue;
     const float Dx = -d / den;
     if (!(Dx > 0.f) || !isfinite(Dx)) continue;
-    float3 c;
+    float4 c;
     if (!plane_c(a.Kinv, make_float4(nq.x, nq.y, nq.z, Dx), ray, &c)) continue;
-    sm.cc(g, 0) = c.x;
-    sm.cc(g, 1) = c.y;
-    sm.cc(g, 2) = c.z;
+    sm.cc(g) = c;
     hD[g] = Dx;
     valid |= 1u << g;
   }
 
   RefWin rw;
-  load_ref_window<kHalf>(a, x, y, rw);
+  if (live) load_ref_window<kHalf>(a, x, y, rw);
 
   // --- Eq. (1): the 8 x N cost matrix (views outer: the 8 hypotheses of a view
   // fetch neighbouring texels) -------------------------------------------------------
-  for (int j = 0; j < N; j++) {
-    const ViewConst& V = a.v[j];
+  if constexpr (kStaged) {
+    // one shared-memory box per view for the whole block, placed where a few
+    // of the pixels' own planes put their windows
+    float4 c_own = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool own_ok = live && plane_c(a.Kinv, a.plane[pi], ray, &c_own);
+    place_boxes(a, *ss, c_own, own_ok, ray);
+    for (int j = 0; j < N; j++) {
+      const ViewConst& V = a.v[j];
+      const BoxPlace bp = ss->place[j];
+      __syncthreads();                      // the previous view's box is no longer read
+      fill_box(V, ss->box, bp);
+      __syncthreads();
+      const uint32_t adj = box_adjust(bp);
 #pragma unroll 1
-    for (int g = 0; g < kRegions; g++) {
-      const bool ok = valid >> g & 1u;
-      const float3 c = ok ? make_float3(sm.cc(g, 0), sm.cc(g, 1), sm.cc(g, 2)) : make_float3(0.f, 0.f, 0.f);
-      sm.m(g, j, N) = ncc_cost<kHalf, kTex>(V, c, ok, fx, fy, rw, npairs);
+      for (int g = 0; g < kRegions; g++) {
+        const bool ok = valid >> g & 1u;
+        const float4 c = ok ? sm.cc(g) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float m = ncc_cost_boxed<kHalf>(V, c, ok, ray, rw, npairs, bp, ss->box, adj);
+        if (live) sm.m(g, j, N) = m;
+      }
+    }
+    if (!live) return;
+  } else {
+    for (int j = 0; j < N; j++) {
+      const ViewConst& V = a.v[j];
+#pragma unroll 1
+      for (int g = 0; g < kRegions; g++) {
+        const bool ok = valid >> g & 1u;
+        const float4 c = ok ? sm.cc(g) : make_float4(0.f, 0.f, 0.f, 0.f);
+        sm.m(g, j, N) = ncc_cost<kHalf, kTex>(V, c, ok, ray, rw, npairs);
+      }
     }
   }
 
   if (kMode & kHeuristic) {
     const int k = a.k < N ? a.k : N;
     float4 best = a.plane[pi];
-    float3 c;
+    float4 c;
     bool ok = plane_c(a.Kinv, best, ray, &c);
-    for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs);
+    for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, ray, rw, npairs);
     float bm = kbest_mean(sm.w, N, k);
     int choice = 8;
     float bestD = 0.f;
@@ -477,7 +710,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 #pragma unroll 1
     for (int ci = 0; ci < nc; ci++) {
       ok = plane_c(a.Kinv, refine_candidate(a, x, y, best, ray, ci), ray, &c);
-      for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs);
+      for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, ray, rw, npairs);
       const float m = kbest_mean(sm.w, N, k);
       if (bc < 0 || m < bcm) { bc = ci; bcm = m; }
     }
@@ -511,12 +744,12 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 
   // --- Eq. (7): unified cost; the own plane competes and wins ties -------------------
   float4 best = a.plane[pi];
-  float3 c;
+  float4 c;
   bool ok = plane_c(a.Kinv, best, ray, &c);
   float bm = 0.f;
   for (int j = 0; j < N; j++) {   // views with weight 0 are skipped (per-lane predicate)
     const float wj = sm.wt(j);
-    if (wj > 0.f) bm = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs), bm);
+    if (wj > 0.f) bm = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, ray, rw, npairs), bm);
   }
   bm *= inv_sw;
   int choice = 8;
@@ -570,7 +803,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     for (int j = 0; j < N; j++) {   // j stays warp-uniform (one texture per gather)
       const float wj = sm.wt(j);
       if (wj > 0.f && alive) {
-        m = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs), m);
+        m = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, ray, rw, npairs), m);
         alive = m * inv_sw < bound;
       }
     }
@@ -604,11 +837,11 @@ __device__ __forceinline__ void init_pixel(const A& a, PixelArrays& sm, int x, i
   const uint4 r = philox4x32_10(make_uint4((uint32_t)pi, 0u, 0u, 0u), a.key0, a.key1);
   const float3 n = face_camera(normal_from_uniforms(u01(r.y), u01(r.z)), ray);
   const float4 pl = make_float4(n.x, n.y, n.z, a.dmin + (a.dmax - a.dmin) * u01(r.x));
-  float3 c;
+  float4 c;
   const bool ok = plane_c(a.Kinv, pl, ray, &c);
   RefWin rw;
   load_ref_window<kHalf>(a, x, y, rw);
-  for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, fx, fy, rw, npairs);
+  for (int j = 0; j < N; j++) sm.wt(j) = ncc_cost<kHalf, kTex>(a.v[j], c, ok, ray, rw, npairs);
   // mean of the k smallest per-view costs, summed in ascending order (ties:
   // lower view index)
   const int k = a.k < N ? a.k : N;

@@ -11,7 +11,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from parity_utils import COST_TOL, FRACTION, TIE_TOL, same_plane
+from parity_utils import COST_TOL, FRACTION, FRACTION_TEXTURE_FILTER, TIE_TOL, same_plane
 
 pytestmark = pytest.mark.gpu
 
@@ -84,4 +84,66 @@ def test_full_size_sampled_phase(oracle_mod, amh, large_scene, t, color, form):
     print(f"\nfull size t={t} colour={color} {form} form: {n} pixels, same plane and |dcost|<=1e-4 on {n_ok}, "
           f"near-ties {n_tie}; |dcost| on same plane: median {np.median(dc):.2e}, "
           f"99.9% {np.quantile(dc, 0.999):.2e}, max {dc.max():.2e}")
-    assert frac >= FRACTION, (n_ok, n_tie, n)
+    assert frac >= (FRACTION_TEXTURE_FILTER if form == "texture" else FRACTION), (n_ok, n_tie, n)
+
+
+def test_full_size_whole_run_depth_parity(oracle_mod, amh, large_scene):
+    """The whole run at the benchmark's size: random init + 6 iterations of
+    the 3200x2112 reference with 10 sources on the GPU (the launch
+    configuration bench.py times) and on the FP64 oracle (the rows of each
+    phase split over the host's cores; results identical to one thread),
+    from the same seed.  The initial costs agree (|dcost| <= 1e-4) on >=
+    99.9 % of all pixels, and the final depth lies within 1 % of the
+    oracle's on >= 99 % of the valid pixels (ground truth hit, >= 5 px from
+    the border).
+
+    Initial costs: both sides draw the same random plane (Philox), the GPU
+    keeps it in FP32.  Random planes include nearly edge-on ones whose
+    windows stretch over hundreds of pixels, where that rounding alone moves
+    a view's cost between a value and 2 (window centre on the view's border,
+    the plane turning behind the view).  Where the two costs differ, the
+    oracle therefore also scores the GPU's own FP32 plane (the mean of its k
+    smallest per-view costs, as the initial cost is defined): the GPU agrees
+    with the oracle at a pixel when its cost is within 1e-4 of the oracle's
+    cost of either plane."""
+    import os
+    import time
+
+    from parity_utils import valid_pixels
+    sc = large_scene
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    g = amh.Context.from_scene(sc, seed=29)
+    o = oracle_mod.Oracle.from_scene(sc, seed=29)
+    oracle_mod.set_threads(threads)
+    try:
+        g.init_random()
+        o.init_random()
+        gi, oi = g.get_state(), o.get_state()
+        d0 = np.abs(gi["cost"].astype(np.float64) - oi["cost"])
+        k = oracle_mod.default_params().k
+        bad = np.argwhere(d0 > COST_TOL)
+        rescored = 0
+        for (y, x) in bad:
+            gp = gi["plane"][y, x].astype(np.float64)
+            per_view = sorted(o.cost(int(x), int(y), gp, j) for j in range(len(sc.src)))
+            if abs(float(np.mean(per_view[:k])) - float(gi["cost"][y, x])) <= COST_TOL:
+                rescored += 1
+        frac_init = 1.0 - (len(bad) - rescored) / d0.size
+        t0 = time.time()
+        o.iterate(6)
+        t_orc = time.time() - t0
+        g.iterate(6)
+        Do = o.depth_map()
+        Dg = g.read_maps()["depth"].astype(np.float64)
+    finally:
+        oracle_mod.set_threads(1)
+    m = valid_pixels(sc)
+    rel = np.abs(Dg - Do) / Do
+    frac = float((rel[m] <= 0.01).mean())
+    print(f"\nfull-size whole run: initial cost agrees on {100 * frac_init:.3f} % of {d0.size} pixels "
+          f"({len(bad)} differ from the oracle's plane by > 1e-4, {rescored} of them match the oracle's cost "
+          f"of the GPU's FP32 plane; max difference {d0.max():.2e}); "
+          f"final depth within 1 % of the oracle on {100 * frac:.3f} % of {int(m.sum())} valid pixels; "
+          f"oracle 6 iterations {t_orc:.0f} s on {threads} threads")
+    assert frac_init >= FRACTION, frac_init
+    assert frac >= 0.99, frac
