@@ -61,6 +61,8 @@ KNOWN_TRAFFIC: dict[str, float] = {
 
 
 PHASE_KERNEL_SOURCES = ("amh_device.cuh", "amh_kernels.cu", "amh_kernels.h", "amh_update.cuh")
+# the batched form's variants (AMH_BATCH_VARIANTS): block tile / warp pixel layout
+VARIANT_NAMES = ["16x16/warp 16x4", "32x8/warp 32x2", "64x4/warp 64x1", "16x16/warp 8x8", "32x8/warp 16x4"]
 
 
 def kernel_source_hash() -> str:
@@ -599,7 +601,7 @@ def bench_batch(args, dist):
             "texture_bilinear": texture,
             "value": round(px * ITERS * steps / (ms / 1e3) / 1e6, 3), "ms_per_batch": round(ms / steps, 3),
             "pixels_per_iteration": px, "pairs_per_batch": pairs, "launches_per_batch": 1 + 2 * ITERS,
-            "tile_variant": ["16x16", "32x8", "64x4"][chosen],
+            "tile_variant": VARIANT_NAMES[chosen], "variants": VARIANT_NAMES,
             "autotune_ms": [round(float(m), 3) for m in tune_ms], "timing": "host wall clock around graph launches"}
 
 

@@ -225,13 +225,22 @@ AMH_API int amh_batch_iterate(amh_batch* batch, int32_t k);
 /* initialisation + iters iterations replayed from a CUDA graph; the graph is
  * captured on the first call for a given iters / tile variant and reused. */
 AMH_API int amh_batch_run(amh_batch* batch, int32_t iters);
-/* Tile variant of the phase kernel: 0 = 16 x 16, 1 = 32 x 8, 2 = 64 x 4
- * pixels per block (8, 16 or 32 same-coloured pixels per row). */
+/* Variant of the phase kernel: the block's tile and each warp's pixel
+ * layout (a warp updates 32 pixels of one colour, laid out in its own
+ * sub-tile of the block's tile; the layout sets how far apart its lanes'
+ * windows fall in every source view):
+ *   0: 16 x 16 tile, warps of 8 x 4 pixels of the colour (16 x 4 pixels)
+ *   1: 32 x 8 tile,  warps of 16 x 2 (32 x 2 pixels)
+ *   2: 64 x 4 tile,  warps of 32 x 1 (64 x 1 pixels)
+ *   3: 16 x 16 tile, warps of 4 x 8 (8 x 8 pixels)
+ *   4: 32 x 8 tile,  warps of 8 x 4 (16 x 4 pixels)
+ * Results do not depend on the variant. */
+#define AMH_BATCH_VARIANTS 5
 AMH_API int amh_batch_set_variant(amh_batch* batch, int32_t variant);
-/* Times initialisation + iters iterations with each tile variant on this
- * batch and keeps the fastest; *chosen gets its index and ms_out[0..2] (may
- * be NULL) the times.  The state afterwards is a tuning run: initialise
- * again before use. */
+/* Times initialisation + iters iterations with each variant on this batch
+ * and keeps the fastest; *chosen gets its index and ms_out[0 ..
+ * AMH_BATCH_VARIANTS - 1] (may be NULL) the times.  The state afterwards is
+ * a tuning run: initialise again before use. */
 AMH_API int amh_batch_autotune(amh_batch* batch, int32_t iters, int32_t* chosen, float* ms_out);
 /* size and number of sources of reference r; *n_refs the batch size */
 AMH_API int amh_batch_info(const amh_batch* batch, int32_t r, int32_t* width, int32_t* height,

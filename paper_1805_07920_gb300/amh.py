@@ -25,6 +25,7 @@ AMH_FLAG_TEXTURE_BILINEAR = 16       # precision form: texture-unit bilinear int
 AMH_FLAG_STAGED_FETCH = 32           # fetch path: shared-memory staged matrix sweep (measured alternative)
 MAX_SRC = 32
 NOALLOC_MAX_PIXELS = 262144
+BATCH_VARIANTS = 5                   # AMH_BATCH_VARIANTS: tile / warp-layout variants of the batched form
 
 EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_random",
            "amh_step_phase", "amh_iterate", "amh_get_state", "amh_set_state", "amh_read_maps",
@@ -462,7 +463,7 @@ class Batch:
 
     def autotune(self, iters=1):
         ch = _i32()
-        ms = (ctypes.c_float * 3)()
+        ms = (ctypes.c_float * BATCH_VARIANTS)()
         self._check(_batch_lib().amh_batch_autotune(self.ctx, int(iters), ctypes.byref(ch), ms))
         return ch.value, list(ms)
 

@@ -5,8 +5,10 @@
 // by timing the candidates on the batch itself.
 //
 // Work items are tiles of one reference, ordered reference by reference; a
-// persistent grid (a few blocks per SM) walks them with a fixed stride, so the
-// schedule is static and deterministic.  A block loads the argument block of
+// persistent grid (a few blocks per SM) takes them in order from one counter,
+// so every block stays busy until the last item (the result of each pixel
+// depends only on its reference's state, not on which block updates it).  A
+// block loads the argument block of
 // its item's reference (sizes, intrinsics, state pointers, view table) into
 // shared memory and runs the same per-pixel update as the single-reference
 // kernels (amh_update.cuh).
@@ -63,24 +65,42 @@ struct BatchArgs {
   int n_refs, n_items, color, t;
   float tau;
   unsigned long long* pairs;
+  unsigned int* queue;   // next work item; zeroed before every launch
 };
 
-// Tile of TW x TH pixels of one colour per 128-thread block: TW / 2 pixels of
-// the colour per row, TH = 256 / TW rows.
-template <int TW>
+// The next work item of this block: blocks take items in order from one
+// counter (balanced to the last item, whatever each item costs).  The whole
+// block calls it; it returns the same item to every thread.
+__device__ __forceinline__ int next_item(const BatchArgs& b, int* slot) {
+  __syncthreads();                       // every thread is done with the previous item
+  if (threadIdx.x == 0) *slot = (int)atomicAdd(b.queue, 1u);
+  __syncthreads();
+  return *slot;
+}
+
+// Tile of TW x TH pixels per 128-thread block, one colour updated: TW / 2
+// pixels of the colour per row, TH = 256 / TW rows.  Each warp takes a
+// sub-tile of WC pixels of the colour per row and 32 / WC rows (its 32
+// pixels laid out WC x 32 / WC), so the tile shape and the warp's pixel
+// layout are chosen independently.
+template <int TW, int WC>
 struct TileShape {
   static constexpr int cols = TW / 2, rows = kBThreads / cols;
+  static constexpr int wrows = 32 / WC, wpr = cols / WC;
+  static_assert(cols % WC == 0 && (cols / WC) * (rows / wrows) == kBThreads / 32, "4 warps tile the block");
+  // (row within the tile, pixel of the colour within the row) of this thread
+  static __device__ __forceinline__ int row(int tid) { return (tid >> 5) / wpr * wrows + (tid & 31) / WC; }
+  static __device__ __forceinline__ int col(int tid) { return (tid >> 5) % wpr * WC + (tid & 31) % WC; }
 };
 
-template <bool kHalf, int TW, int kMode>
+template <bool kHalf, int TW, int WC, int kMode>
 __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ RefArgs ra;
-  __shared__ int cur_ref;
-  using T = TileShape<TW>;
+  __shared__ int cur_ref, item_slot;
+  using T = TileShape<TW, WC>;
   int npairs = 0;
   if (threadIdx.x == 0) cur_ref = -1;
-  for (int item = blockIdx.x; item < b.n_items; item += gridDim.x) {
-    __syncthreads();
+  for (int item = next_item(b, &item_slot); item < b.n_items; item = next_item(b, &item_slot)) {
     // the reference of this item: items are ordered reference by reference
     int r = 0;
     while (r + 1 < b.n_refs && b.refs[r + 1].tile0 <= item) r++;
@@ -100,8 +120,8 @@ __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_
     }
     const int local = item - ra.tile0;
     const int ty = local / ra.tiles_x, tx = local % ra.tiles_x;
-    const int y = ty * T::rows + threadIdx.x / T::cols;
-    const int x = tx * TW + 2 * (threadIdx.x % T::cols) + ((y + b.color) & 1);
+    const int y = ty * T::rows + T::row(threadIdx.x);
+    const int x = tx * TW + 2 * T::col(threadIdx.x) + ((y + b.color) & 1);
     if (x < ra.W && y < ra.H) {
       PixelArrays sm;
       update_pixel<kHalf, kMode>(ra, sm, x, y, &npairs);
@@ -116,11 +136,10 @@ __global__ void __launch_bounds__(kBThreads, 3) batch_phase_kernel(const __grid_
 template <bool kHalf, bool kTex>
 __global__ void __launch_bounds__(kBThreads) batch_init_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ RefArgs ra;
-  __shared__ int cur_ref;
+  __shared__ int cur_ref, item_slot;
   int npairs = 0;
   if (threadIdx.x == 0) cur_ref = -1;
-  for (int item = blockIdx.x; item < b.n_items; item += gridDim.x) {
-    __syncthreads();
+  for (int item = next_item(b, &item_slot); item < b.n_items; item = next_item(b, &item_slot)) {
     int r = 0;
     while (r + 1 < b.n_refs && b.refs[r + 1].tile0 <= item) r++;
     if (r != cur_ref) {
@@ -174,13 +193,14 @@ struct amh_batch {
   uint8_t* d_choice = nullptr;
   std::vector<size_t> px0;                // first pixel of each reference in the state arrays
   ViewConst* d_views = nullptr;
-  RefArgs* d_refs[3] = {nullptr, nullptr, nullptr};   // per tile width variant
-  int items[3] = {0, 0, 0};
+  RefArgs* d_refs[AMH_BATCH_VARIANTS] = {};   // work lists, per variant (by its tile width)
+  int items[AMH_BATCH_VARIANTS] = {};
   int init_items = 0;
   RefArgs* d_refs_init = nullptr;
   unsigned long long* d_pairs = nullptr;
   unsigned int* d_status = nullptr;       // bounds-check status word (bounds-checked builds)
-  int variant = 0;                        // tile width 16, 32, 64
+  unsigned int* d_queue = nullptr;        // work-item counter of the running launch
+  int variant = 0;                        // index into kVariants
   int t = 0;
   bool initialized = false;
   int grid_blocks = 0;
@@ -190,7 +210,10 @@ struct amh_batch {
 };
 
 namespace {
-const int kTileW[3] = {16, 32, 64};
+// the phase kernel's variants: (tile width in pixels, warp width in pixels of
+// the colour); the block is always 128 threads, 256 pixels
+struct Variant { int tw, wc; };
+const Variant kVariants[AMH_BATCH_VARIANTS] = {{16, 8}, {32, 16}, {64, 32}, {16, 4}, {32, 8}};
 thread_local std::string g_batch_create_err;
 
 int bfail(amh_batch* b, int code, const char* fmt, ...) {
@@ -252,6 +275,7 @@ void free_batch(amh_batch* b) {
   cudaFree(b->d_refs_init);
   cudaFree(b->d_pairs);
   cudaFree(b->d_status);
+  cudaFree(b->d_queue);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -266,16 +290,21 @@ BatchArgs make_args(amh_batch* b, const RefArgs* refs, int n_items, int color) {
   a.t = b->t;
   a.tau = tau_at(b->p, b->t);
   a.pairs = b->d_pairs;
+  a.queue = b->d_queue;
   return a;
 }
 
 template <bool kHalf, int kMode>
 void launch_batch_phase(amh_batch* b, int color) {
   const BatchArgs a = make_args(b, b->d_refs[b->variant], b->items[b->variant], color);
-  switch (kTileW[b->variant]) {
-    case 16: batch_phase_kernel<kHalf, 16, kMode><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
-    case 32: batch_phase_kernel<kHalf, 32, kMode><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
-    default: batch_phase_kernel<kHalf, 64, kMode><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a); break;
+  cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), b->stream);
+  const dim3 g(b->grid_blocks), t(kBThreads);
+  switch (b->variant) {
+    case 0: batch_phase_kernel<kHalf, 16, 8, kMode><<<g, t, 0, b->stream>>>(a); break;
+    case 1: batch_phase_kernel<kHalf, 32, 16, kMode><<<g, t, 0, b->stream>>>(a); break;
+    case 2: batch_phase_kernel<kHalf, 64, 32, kMode><<<g, t, 0, b->stream>>>(a); break;
+    case 3: batch_phase_kernel<kHalf, 16, 4, kMode><<<g, t, 0, b->stream>>>(a); break;
+    default: batch_phase_kernel<kHalf, 32, 8, kMode><<<g, t, 0, b->stream>>>(a); break;
   }
 }
 // FP16 images, uint8 images, or uint8 images through the texture unit's
@@ -292,6 +321,7 @@ int batch_phase(amh_batch* b, int color) {
 int batch_init(amh_batch* b) {
   b->t = 0;
   const BatchArgs a = make_args(b, b->d_refs_init, b->init_items, 0);
+  cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), b->stream);
   if (b->tex_filter) batch_init_kernel<false, true><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
   else if (b->half) batch_init_kernel<true, false><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
   else batch_init_kernel<false, false><<<b->grid_blocks, kBThreads, 0, b->stream>>>(a);
@@ -422,6 +452,7 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
   CB(cudaMemsetAsync(b->d_pairs, 0, kPairCounters * sizeof(unsigned long long), b->stream));
   CB(cudaMalloc(&b->d_status, sizeof(unsigned int)));
   CB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), b->stream));
+  CB(cudaMalloc(&b->d_queue, sizeof(unsigned int)));
   for (int r = 0; r < n_refs; r++) {
     const amh_camera& cr = cams[refs[r]];
     double Kri[9];
@@ -510,7 +541,8 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(b->stream);   // h goes out of scope
   };
-  for (int vi = 0; vi < 3; vi++) CB(upload(kTileW[vi], 2 * kBThreads / kTileW[vi], &b->d_refs[vi], &b->items[vi]));
+  for (int vi = 0; vi < AMH_BATCH_VARIANTS; vi++)
+    CB(upload(kVariants[vi].tw, 2 * kBThreads / kVariants[vi].tw, &b->d_refs[vi], &b->items[vi]));
   CB(upload(16, 8, &b->d_refs_init, &b->init_items));
   int dev = 0, sms = 0;
   CB(cudaGetDevice(&dev));
@@ -581,7 +613,8 @@ AMH_API int amh_batch_run(amh_batch* b, int32_t iters) {
 
 AMH_API int amh_batch_set_variant(amh_batch* b, int32_t variant) {
   if (!b) return AMH_EINVAL;
-  if (variant < 0 || variant > 2) return bfail(b, AMH_EINVAL, "variant must be 0 (16 px), 1 (32 px) or 2 (64 px)");
+  if (variant < 0 || variant >= AMH_BATCH_VARIANTS)
+    return bfail(b, AMH_EINVAL, "variant must be 0 .. %d", AMH_BATCH_VARIANTS - 1);
   b->variant = variant;
   return AMH_OK;
 }
@@ -594,7 +627,7 @@ AMH_API int amh_batch_autotune(amh_batch* b, int32_t iters, int32_t* chosen, flo
   BTRY(b, cudaEventCreate(&e1));
   float best = 0.f;
   int bi = 0;
-  for (int vi = 0; vi < 3; vi++) {
+  for (int vi = 0; vi < AMH_BATCH_VARIANTS; vi++) {
     b->variant = vi;
     int rc = batch_init(b);
     for (int i = 0; i < iters && !rc; i++) rc = batch_phase(b, i & 1);   // warm-up

@@ -81,7 +81,7 @@ def test_graph_replay_and_variants_agree(amh, ring, synth_mod):
     b.init_random()
     b.iterate(3)
     ref_states = [b.get_state(r) for r in refs]
-    for variant in (0, 1, 2):
+    for variant in range(amh.BATCH_VARIANTS):
         b.set_variant(variant)
         b.run(3)            # init + 3 iterations from a CUDA graph
         b.run(3)            # replayed
@@ -97,7 +97,7 @@ def test_autotune_picks_a_variant(amh, ring, synth_mod):
     p = amh.default_params(depth_min=ring.depth_min, depth_max=ring.depth_max, seed=72)
     b = amh.Batch(ring.cams, ring.images, refs, srcs, p)
     chosen, ms = b.autotune(iters=1)
-    assert chosen in (0, 1, 2)
+    assert chosen in range(amh.BATCH_VARIANTS) and len(ms) == amh.BATCH_VARIANTS
     assert all(m > 0 for m in ms) and ms[chosen] == min(ms)
     with pytest.raises(amh.AmhError):
         b.step_phase(0)     # the tuning run left no usable state
@@ -112,9 +112,12 @@ def test_batch_rejects_bad_lists(amh, ring):
         amh.Batch(ring.cams, ring.images, [0, 1], [[1, 2], [1, 3]])   # ref 1 lists itself
     with pytest.raises(amh.AmhError):
         amh.Batch(ring.cams, ring.images, [0], [[]])                  # no source
+    b = amh.Batch(ring.cams, ring.images, [0], [[1]])
+    with pytest.raises(amh.AmhError):
+        b.set_variant(amh.BATCH_VARIANTS)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_batch_phases_match_oracle(amh, oracle_mod, synth_mod, variant):
     """The batched kernel against the FP64 oracle directly: three references
     of uneven, ragged sizes in one batch, each tile variant, the state first

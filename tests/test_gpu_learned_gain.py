@@ -5,16 +5,19 @@ trained by the library's own kernels on the plain method's outputs for 200
 seeded 1600x1056 scenes (seeds 1000-1199; validation 1900-1905) and the
 proposal schedule (network on the state after 2 iterations, its plane scored
 during the third) and the training resolution were picked on scenes
-2000-2002.  Here two further held-out
-scenes at 1600x1056 with 10 sources (seeds 2003, 2004) are run with and
-without the proposal from the same random initialisation.  Accuracy is the
-fraction of valid pixels with depth within 1 % of the ground truth (valid:
-ground truth present, >= 5 px from the border).
+2000-2002 (seed 2005 served the ablation table).  Here seven further
+held-out scenes at 1600x1056 with 10 sources (seeds 2003, 2004, 2006-2010),
+none used by any choice, are run with and without the proposal from the same
+random initialisation.  Accuracy is the fraction of valid pixels with depth
+within 1 % of the ground truth (valid: ground truth present, >= 5 px from
+the border).
 
 Shown: from the injected iteration on the learned run is never behind the
 plain one, it ends ahead, and it reaches the plain method's 6-iteration
-accuracy in fewer iterations on both scenes (the device times of both
-paths, network included, are printed)."""
+accuracy in fewer iterations on every scene; the margin at that crossing and
+the iteration count and device time to the plain method's iteration-3
+accuracy are printed (there the proposal gains no iteration: it is scored in
+the third iteration itself)."""
 import numpy as np
 import pytest
 
@@ -38,16 +41,20 @@ def test_trained_network_gain(amh, synth_mod):
     net.load(LE.WEIGHTS)
     sched = {"net@2": LE.SCHEDULES["net@2"]}
     iters_to = []
-    for seed in (2003, 2004):
+    for seed in (2003, 2004, 2006, 2007, 2008, 2009, 2010):
         sc = synth_mod.make_scene("learned", seed=seed)
         r = LE.evaluate_scene(sc, net, seed, schedules=sched, log=lambda s: None)
         s = r["schedules"]["net@2"]
         ap, al = np.array(r["acc_plain"]), np.array(s["acc"])
+        k = s["iters_to_plain_final"]
+        k3 = next((i + 1 for i, a in enumerate(al) if a >= ap[2]), None)
+        margin = al[k - 1] - ap[-1] if k else float("nan")
         print(f"seed {seed}: plain {np.round(ap, 4).tolist()} ({r['ms_plain_final']:.1f} ms for 6 iterations); "
-              f"with proposal {np.round(al, 4).tolist()}; plain's final accuracy after "
-              f"{s['iters_to_plain_final']} iterations, {s['ms_to_plain_final'] or float('nan'):.1f} ms")
+              f"with proposal {np.round(al, 4).tolist()}; plain's final accuracy after {k} iterations, "
+              f"{s['ms_to_plain_final'] or float('nan'):.1f} ms, margin {margin:.1e}; plain's iteration-3 "
+              f"accuracy after {k3} iterations")
         np.testing.assert_array_equal(al[:2], ap[:2])      # identical until the proposal is scored
         assert (al[2:] >= ap[2:] - 1e-4).all()
         assert al[-1] > ap[-1]
-        iters_to.append(s["iters_to_plain_final"] or 99)
-    assert max(iters_to) <= 5          # fewer iterations than the plain method's 6 on both scenes
+        iters_to.append(k or 99)
+    assert max(iters_to) <= 5          # fewer iterations than the plain method's 6 on every scene
