@@ -5,12 +5,14 @@
 // with the unchanged matching cost (Eq. 8) and view weights (Eqs. 2-7) as one
 // more candidate, so the plain method stays the arbiter.
 //
-// Kernels: 3x3 convolution forward on tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation, fused bias / ReLU / skip add), the data
+// Kernels: 3x3 convolution forward on the fifth-generation tensor cores
+// (tcgen05.mma, FP32 accumulator in tensor memory, BF16 operands brought in by
+// the tensor memory accelerator; fused bias / ReLU / skip add), the data
 // gradient as the same convolution with flipped, transposed weights, the
-// weight gradient on tensor cores as well (BF16 operands, FP32 accumulation;
-// bias gradients in FP32), 2x2 average pooling, nearest upsampling, the L1
-// loss, Adam, and the feature / head / proposal conversions.
+// weight gradient on the same tensor-core path from channel-major copies of
+// the operands (amh_conv_tc.cuh; bias gradients in FP32), 2x2 average pooling,
+// nearest upsampling, the L1 loss, Adam, and the feature / head / proposal
+// conversions.
 //
 // Layout: activations (H, W, C) with C a multiple of 16, BF16 between
 // layers; conv weights (9, Cout, Cin) BF16 (FP32 master copy for Adam), tap
@@ -28,7 +30,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "amh.h"
+#include "amh_conv_tc.cuh"
 #include "amh_ctx.h"
 #include "amh_device.cuh"
 
@@ -40,160 +45,6 @@ struct LayerDef { int cin, cout, relu; };
 // e1 e2 e3 e4 d3 d2 d1 out
 constexpr LayerDef kNet[kLayers] = {{16, 32, 1}, {32, 64, 1}, {64, 96, 1}, {96, 128, 1},
                                     {128, 96, 1}, {96, 64, 1}, {64, 32, 1}, {32, 16, 0}};
-
-// ---------------------------------------------------------------------------
-// tensor-core 3x3 convolution: a block computes 64 pixels of one row x 32
-// output channels; warp w takes pixels 16 w .. 16 w + 15 (one m16 tile) and
-// the 4 n8 tiles.  The block's weights sit in shared memory, rows padded by 8
-// BF16 so the B-fragment loads are conflict-free.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-struct ConvArgs {
-  const __nv_bfloat16* x;    // (H, W, Cin)
-  const __nv_bfloat16* w;    // (9, Cout, Cin)
-  const float* bias;         // Cout or null
-  const __nv_bfloat16* skip; // (H, W, Cout) added after the ReLU, or null
-  __nv_bfloat16* y16;        // (H, W, Cout) BF16 output (after ReLU + skip), or null
-  __nv_bfloat16* r16;        // (H, W, Cout) ReLU output before the skip, or null
-  float* y32;                // (H, W, Cout) FP32 output, or null
-  int H, W, Cin, Cout, relu;
-};
-
-__global__ void __launch_bounds__(128) conv3x3_fwd_kernel(const ConvArgs a) {
-  extern __shared__ __nv_bfloat16 ws[];   // [9][32][Cin + 8]
-  const int ld = a.Cin + 8;
-  const int co0 = blockIdx.z * 32;
-  const int y = blockIdx.y, x0 = blockIdx.x * 64;
-  for (int i = threadIdx.x; i < 9 * 32 * a.Cin; i += blockDim.x) {
-    const int t = i / (32 * a.Cin), r = (i / a.Cin) % 32, ci = i % a.Cin;
-    const int co = co0 + r;
-    ws[(t * 32 + r) * ld + ci] = co < a.Cout ? a.w[((size_t)t * a.Cout + co) * a.Cin + ci] : __float2bfloat16(0.f);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, tq = lane & 3;
-  const int px0 = x0 + warp * 16 + g, px1 = px0 + 8;
-  float acc[4][4];
-#pragma unroll
-  for (int n = 0; n < 4; n++)
-#pragma unroll
-    for (int e = 0; e < 4; e++) acc[n][e] = 0.f;
-  for (int t = 0; t < 9; t++) {
-    const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const int yy = y + dy;
-    const int xa = px0 + dx, xb = px1 + dx;
-    const bool rowok = yy >= 0 && yy < a.H;
-    const bool oka = rowok && xa >= 0 && xa < a.W, okb = rowok && xb >= 0 && xb < a.W;
-    const uint32_t* pa = reinterpret_cast<const uint32_t*>(a.x + (oka ? ((size_t)yy * a.W + xa) * a.Cin : 0));
-    const uint32_t* pb = reinterpret_cast<const uint32_t*>(a.x + (okb ? ((size_t)yy * a.W + xb) * a.Cin : 0));
-    const __nv_bfloat16* wt = ws + (size_t)t * 32 * ld;
-    for (int c0 = 0; c0 < a.Cin; c0 += 16) {
-      uint32_t af[4];
-      af[0] = oka ? __ldg(pa + (c0 >> 1) + tq) : 0u;
-      af[1] = okb ? __ldg(pb + (c0 >> 1) + tq) : 0u;
-      af[2] = oka ? __ldg(pa + (c0 >> 1) + tq + 4) : 0u;
-      af[3] = okb ? __ldg(pb + (c0 >> 1) + tq + 4) : 0u;
-#pragma unroll
-      for (int n = 0; n < 4; n++) {
-        const __nv_bfloat16* wr = wt + (n * 8 + g) * ld + c0 + 2 * tq;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 8);
-        mma_bf16(acc[n], af, b0, b1);
-      }
-    }
-  }
-  // epilogue: (row g -> pixel px0, row g + 8 -> px1), columns 2 tq, 2 tq + 1
-#pragma unroll
-  for (int n = 0; n < 4; n++) {
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      const int px = e < 2 ? px0 : px1;
-      const int co = co0 + n * 8 + 2 * tq + (e & 1);
-      if (px >= a.W || co >= a.Cout) continue;
-      float v = acc[n][e] + (a.bias ? a.bias[co] : 0.f);
-      if (a.relu) v = fmaxf(v, 0.f);
-      const size_t o = ((size_t)y * a.W + px) * a.Cout + co;
-      if (a.r16) a.r16[o] = __float2bfloat16(v);
-      if (a.skip) v = __bfloat162float(__float2bfloat16(v)) + __bfloat162float(a.skip[o]);
-      if (a.y16) a.y16[o] = __float2bfloat16(v);
-      if (a.y32) a.y32[o] = v;
-    }
-  }
-}
-
-// Weight gradient on tensor cores: dW[t] (Cout x Cin) = sum over pixels p of
-// dy(p)^T x(p + off(t)), BF16 operands (the BF16 copy of dy the data gradient
-// uses too), FP32 accumulation.  A block owns one tap and a 32 x 32 (co, ci)
-// tile and sums the chunks of kWgChunk pixels chunk0, chunk0 + stride, ...:
-// each chunk is staged transposed in shared memory (channel rows, pixel
-// columns, rows padded by 8 BF16 so the fragment loads are conflict-free);
-// warp w computes co (w / 2) * 16 .. + 15 x ci (w % 2) * 16 .. + 15 as one m16
-// tile and two n8 tiles.  The partial tiles meet in dw by atomics.
-constexpr int kWgChunk = 64;
-constexpr int kWgLd = kWgChunk + 8;
-__global__ void __launch_bounds__(128) conv3x3_wgrad_kernel(const __nv_bfloat16* __restrict__ x,
-                                                           const __nv_bfloat16* __restrict__ dy, float* dw,
-                                                           int H, int W, int Cin, int Cout) {
-  __shared__ __align__(16) __nv_bfloat16 sdy[32 * kWgLd];   // [co][px]
-  __shared__ __align__(16) __nv_bfloat16 sx[32 * kWgLd];    // [ci][px]
-  const int t = blockIdx.z % 9, stride = gridDim.z / 9;
-  const int co0 = blockIdx.y * 32, ci0 = blockIdx.x * 32;
-  const int oy = t / 3 - 1, ox = t % 3 - 1;
-  const int np = H * W, nchunks = (np + kWgChunk - 1) / kWgChunk;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, tq = lane & 3;
-  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
-  float acc[2][4];
-#pragma unroll
-  for (int nt = 0; nt < 2; nt++)
-#pragma unroll
-    for (int e = 0; e < 4; e++) acc[nt][e] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int chunk = blockIdx.z / 9; chunk < nchunks; chunk += stride) {
-    const int p0 = chunk * kWgChunk;
-    __syncthreads();
-    for (int i = threadIdx.x; i < kWgChunk * 32; i += blockDim.x) {
-      const int px = i / 32, c = i % 32;
-      const int p = p0 + px;
-      __nv_bfloat16 vdy = zero, vx = zero;
-      if (p < np) {
-        if (co0 + c < Cout) vdy = dy[(size_t)p * Cout + co0 + c];
-        const int qy = p / W + oy, qx = p % W + ox;
-        if (ci0 + c < Cin && qy >= 0 && qy < H && qx >= 0 && qx < W) vx = x[((size_t)qy * W + qx) * Cin + ci0 + c];
-      }
-      sdy[c * kWgLd + px] = vdy;
-      sx[c * kWgLd + px] = vx;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k0 = 0; k0 < kWgChunk; k0 += 16) {
-      uint32_t af[4];
-      af[0] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g) * kWgLd + k0 + 2 * tq]);
-      af[1] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g + 8) * kWgLd + k0 + 2 * tq]);
-      af[2] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g) * kWgLd + k0 + 2 * tq + 8]);
-      af[3] = *reinterpret_cast<const uint32_t*>(&sdy[(m0 + g + 8) * kWgLd + k0 + 2 * tq + 8]);
-#pragma unroll
-      for (int nt = 0; nt < 2; nt++) {
-        const __nv_bfloat16* br = &sx[(n0 + nt * 8 + g) * kWgLd + k0 + 2 * tq];
-        mma_bf16(acc[nt], af, *reinterpret_cast<const uint32_t*>(br), *reinterpret_cast<const uint32_t*>(br + 8));
-      }
-    }
-  }
-#pragma unroll
-  for (int nt = 0; nt < 2; nt++)
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      const int co = co0 + m0 + g + (e >= 2 ? 8 : 0), ci = ci0 + n0 + nt * 8 + 2 * tq + (e & 1);
-      if (co < Cout && ci < Cin) atomicAdd(&dw[((size_t)t * Cout + co) * Cin + ci], acc[nt][e]);
-    }
-}
 
 // bias gradient in FP32: db[c] = sum over pixels of dy(p, c)
 __global__ void __launch_bounds__(256) bias_grad_kernel(const float* __restrict__ dy, int np, int C,
@@ -403,6 +254,11 @@ struct amh_net {
   float* dy[kLayers] = {};
   float *gA = nullptr, *gB = nullptr, *gE1 = nullptr, *gE2 = nullptr, *gE3 = nullptr;
   float* loss = nullptr;
+  unsigned int* status = nullptr;         // bit 0: a convolution's barrier wait gave up
+  // channel-major operands of the weight gradient: x shifted by -1, 0, +1
+  // along the row, and dy
+  __nv_bfloat16* tX[3] = {};
+  __nv_bfloat16* tD = nullptr;
   size_t maxel = 0;
   std::vector<void*> allocs;
   std::string err;
@@ -436,35 +292,99 @@ cudaError_t nalloc(amh_net* n, T** p, size_t count) {
                    cudaGetErrorString(e_));                                                    \
   } while (0)
 
+// the driver's tensor-map encoder, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+// tensor map of a BF16 tensor of dims (d0, d1, d2), d0 contiguous, rows of
+// pitch0 elements (>= d0), read in boxes of (b0, b1, b2); reads outside the
+// tensor return zeros
+bool bf16_map(CUtensorMap* m, const void* p, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+              uint32_t b2 = 1, uint64_t pitch0 = 0) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  if (!pitch0) pitch0 = d0;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {pitch0 * 2, pitch0 * d1 * 2};
+  cuuint32_t box[3] = {b0, b1, b2};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(p), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3x3 convolution on the tensor cores (amh_conv_tc.cuh): x (H, W, Cin), w (9,
+// Cout, Cin), Cin and Cout multiples of 16, Cout at most 128
 int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* skip,
          __nv_bfloat16* y16, __nv_bfloat16* r16, float* y32, int H, int W, int Cin, int Cout, int relu) {
-  ConvArgs a{x, w, bias, skip, y16, r16, y32, H, W, Cin, Cout, relu};
-  const size_t smem = (size_t)9 * 32 * (Cin + 8) * sizeof(__nv_bfloat16);
-  // the largest weight tile (Cin = 128) needs more than the default 48 KB;
-  // the attribute is per device, so set it for each device a network uses
-  static std::once_flag once[64];
+  if (Cin % 16 || Cout % 16 || Cout > tc::kMaxCout) return nfail(n, AMH_EINVAL, "conv: channel counts");
+  CUtensorMap mx, mw;
+  if (!bf16_map(&mx, x, Cin, W, H, 8, tc::kM) || !bf16_map(&mw, w, Cin, Cout, 9, 8, Cout))
+    return nfail(n, AMH_ECUDA, "conv: tensor map encoding failed");
+  const tc::ConvTcArgs a{bias, skip, y16, r16, y32, n->status, H, W, Cin, Cout, relu};
+  // persistent grid: as many CTAs as fit on the SMs at once (every CTA holds
+  // its tensor memory until it exits), at most one per tile
+  static int n_sm[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
+  if (!n_sm[dev & 63]) cudaDeviceGetAttribute(&n_sm[dev & 63], cudaDevAttrMultiProcessorCount, dev);
+  static std::once_flag once[64];
   std::call_once(once[dev & 63], [] {
-    cudaFuncSetAttribute(conv3x3_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 32 * (128 + 8) * 2);
+    cudaFuncSetAttribute(tc::conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes);
   });
-  dim3 grid((W + 63) / 64, H, (Cout + 31) / 32);
-  conv3x3_fwd_kernel<<<grid, 128, smem, n->stream>>>(a);
+  const int ntiles = H * ((W + tc::kM - 1) / tc::kM);
+  const int grid = std::max(1, std::min(ntiles, n_sm[dev & 63] * tc::ctas_per_sm(Cout)));
+  tc::conv3x3_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, n->stream>>>(mx, mw, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
   return AMH_OK;
 }
+// (H, W, C) -> (C, H, Wp) channel-major copy shifted along the row by shift
+// (tc::to_channel_major_kernel)
+void to_cm(amh_net* n, const __nv_bfloat16* in, __nv_bfloat16* out, int H, int W, int Wp, int C, int shift) {
+  const int P = H * W;
+  tc::to_channel_major_kernel<<<dim3((P + 31) / 32, (C + 31) / 32), 256, 0, n->stream>>>(in, out, H, W, Wp, C, shift);
+}
 // weight gradient of layer L from its input x and its output gradient (FP32
-// dy for the bias, its BF16 copy dy16 for the weights)
-void wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, const __nv_bfloat16* dy16, int H, int W) {
-  const int Cin = kNet[L].cin, Cout = kNet[L].cout, np = H * W;
-  // enough blocks to fill the GPU a few times over; each strides over chunks
-  const int tiles = ((Cin + 31) / 32) * ((Cout + 31) / 32), nchunks = (np + kWgChunk - 1) / kWgChunk;
-  const int groups = std::max(1, std::min(nchunks, 2048 / (9 * tiles)));
-  dim3 grid((Cin + 31) / 32, (Cout + 31) / 32, 9 * groups);
-  conv3x3_wgrad_kernel<<<grid, 128, 0, n->stream>>>(x, dy16, n->gw[L], H, W, Cin, Cout);
+// dy for the bias, its BF16 copy dy16 for the weights): both operands are
+// turned channel-major, then the tensor-core kernel sums a band of rows per
+// CTA and tap into gw
+int wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, const __nv_bfloat16* dy16, int H, int W) {
+  const int Cin = kNet[L].cin, Cout = kNet[L].cout, np = H * W, Wp = (W + 7) & ~7;
+  CUtensorMap mdy, mx[3];
+  for (int s = 0; s < 3; s++) {
+    to_cm(n, x, n->tX[s], H, W, Wp, Cin, s - 1);
+    if (!bf16_map(&mx[s], n->tX[s], W, H, Cin, 8, 1, Cin, Wp)) return nfail(n, AMH_ECUDA, "wgrad: tensor map encoding failed");
+  }
+  to_cm(n, dy16, n->tD, H, W, Wp, Cout, 0);
+  if (!bf16_map(&mdy, n->tD, W, H, Cout, 8, 1, Cout, Wp)) return nfail(n, AMH_ECUDA, "wgrad: tensor map encoding failed");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::once_flag once[64];
+  std::call_once(once[dev & 63], [] {
+    cudaFuncSetAttribute(tc::wgrad3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes);
+  });
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // about four CTAs per SM over the 9 taps, whole rows each
+  const int bands = std::max(1, std::min(H, 4 * n_sm / 9)), rows = (H + bands - 1) / bands;
+  const tc::WgradTcArgs a{n->gw[L], n->status, H, W, Cin, Cout, rows};
+  tc::wgrad3x3_tc_kernel<<<dim3((H + rows - 1) / rows, 9), tc::kThreads, tc::kSmemBytes, n->stream>>>(mdy, mx[0], mx[1],
+                                                                                                     mx[2], a);
   const int per_block = 2048, nb = (np + per_block - 1) / per_block;
   bias_grad_kernel<<<dim3((Cout + 31) / 32, nb), 256, 0, n->stream>>>(dy, np, Cout, per_block, n->gb[L]);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "wgrad launch: %s", cudaGetErrorString(e));
+  return AMH_OK;
 }
 // data gradient of layer L: dx (FP32, H x W x Cin) from dy (BF16 copy in g16)
 int dgrad(amh_net* n, int L, const __nv_bfloat16* dy16, float* dx, int H, int W) {
@@ -517,6 +437,7 @@ AMH_API int amh_net_create(amh_net** out, int32_t width2, int32_t height2, uint6
     cudaMemcpyAsync(n->wm[L], w.data(), nw * sizeof(float), cudaMemcpyHostToDevice, n->stream);
     cudaStreamSynchronize(n->stream);
   }
+  NA(n->status, 1);
   const size_t P0 = (size_t)width2 * height2, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
   NA(n->x0, P0 * 16); NA(n->e1, P0 * 32); NA(n->in_e2, P1 * 32); NA(n->e2, P1 * 64); NA(n->in_e3, P2 * 64);
   NA(n->e3, P2 * 96); NA(n->in_e4, P3 * 96); NA(n->e4, P3 * 128); NA(n->in_d3, P2 * 128); NA(n->r3, P2 * 96);
@@ -524,6 +445,7 @@ AMH_API int amh_net_create(amh_net** out, int32_t width2, int32_t height2, uint6
   NA(n->r1, P0 * 32); NA(n->d1, P0 * 32);
   n->maxel = P0 * 64;
   NA(n->g16, n->maxel); NA(n->gA, n->maxel); NA(n->gB, n->maxel);
+  NA(n->tX[0], n->maxel); NA(n->tX[1], n->maxel); NA(n->tX[2], n->maxel); NA(n->tD, n->maxel);
   {
     const size_t lp[kLayers] = {P0, P1, P2, P3, P2, P1, P0, P0};   // output size of each layer
     for (int L = 0; L < kLayers; L++) NA(n->dy[L], lp[L] * kNet[L].cout);
@@ -660,38 +582,38 @@ AMH_API int amh_net_backward(amh_net* n, float* loss_out) {
   l1_loss_kernel<<<blocks_for(P0), 256, 0, s>>>(n->out, n->target, n->mask, dy[7], n->loss, (int)P0, inv_n);
   // out = conv(d1)
   to_bf16_kernel<<<blocks_for(P0 * 16), 256, 0, s>>>(dy[7], n->g16, P0 * 16);
-  wgrad(n, 7, n->d1, dy[7], n->g16, H0, W0);
-  int rc = dgrad(n, 7, n->g16, n->gA, H0, W0);                       // gA = d d1 (P0 x 32)
+  int rc = wgrad(n, 7, n->d1, dy[7], n->g16, H0, W0);
+  if (!rc) rc = dgrad(n, 7, n->g16, n->gA, H0, W0);                  // gA = d d1 (P0 x 32)
   // d1 = relu(conv(in_d1)) + e1
   NTRY(n, cudaMemcpyAsync(n->gE1, n->gA, P0 * 32 * 4, cudaMemcpyDeviceToDevice, s));
   relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gA, n->r1, dy[6], n->g16, P0 * 32);
-  wgrad(n, 6, n->in_d1, dy[6], n->g16, H0, W0);
+  if (!rc) rc = wgrad(n, 6, n->in_d1, dy[6], n->g16, H0, W0);
   if (!rc) rc = dgrad(n, 6, n->g16, n->gA, H0, W0);                  // d in_d1 (P0 x 64)
   up2_bwd_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gA, n->gE2, H1, W1, 64);  // d d2 (P1 x 64)
   relu_mask_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gE2, n->r2, dy[5], n->g16, P1 * 64);
-  wgrad(n, 5, n->in_d2, dy[5], n->g16, H1, W1);
+  if (!rc) rc = wgrad(n, 5, n->in_d2, dy[5], n->g16, H1, W1);
   if (!rc) rc = dgrad(n, 5, n->g16, n->gA, H1, W1);                  // d in_d2 (P1 x 96)
   up2_bwd_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gA, n->gE3, H2, W2, 96);  // d d3 (P2 x 96)
   relu_mask_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gE3, n->r3, dy[4], n->g16, P2 * 96);
-  wgrad(n, 4, n->in_d3, dy[4], n->g16, H2, W2);
+  if (!rc) rc = wgrad(n, 4, n->in_d3, dy[4], n->g16, H2, W2);
   if (!rc) rc = dgrad(n, 4, n->g16, n->gA, H2, W2);                  // d in_d3 (P2 x 128)
   up2_bwd_kernel<<<blocks_for(P3 * 128), 256, 0, s>>>(n->gA, n->gB, H3, W3, 128); // d e4 (P3 x 128)
   // e4 = relu(conv(in_e4))
   relu_mask_kernel<<<blocks_for(P3 * 128), 256, 0, s>>>(n->gB, n->e4, dy[3], n->g16, P3 * 128);
-  wgrad(n, 3, n->in_e4, dy[3], n->g16, H3, W3);
+  if (!rc) rc = wgrad(n, 3, n->in_e4, dy[3], n->g16, H3, W3);
   if (!rc) rc = dgrad(n, 3, n->g16, n->gA, H3, W3);                  // d in_e4 (P3 x 96)
   pool2_bwd_add_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gA, n->gE3, H2, W2, 96);
   // e3 = relu(conv(in_e3)), read by d3 (skip) and by the pooling
   relu_mask_kernel<<<blocks_for(P2 * 96), 256, 0, s>>>(n->gE3, n->e3, dy[2], n->g16, P2 * 96);
-  wgrad(n, 2, n->in_e3, dy[2], n->g16, H2, W2);
+  if (!rc) rc = wgrad(n, 2, n->in_e3, dy[2], n->g16, H2, W2);
   if (!rc) rc = dgrad(n, 2, n->g16, n->gA, H2, W2);                  // d in_e3 (P2 x 64)
   pool2_bwd_add_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gA, n->gE2, H1, W1, 64);
   relu_mask_kernel<<<blocks_for(P1 * 64), 256, 0, s>>>(n->gE2, n->e2, dy[1], n->g16, P1 * 64);
-  wgrad(n, 1, n->in_e2, dy[1], n->g16, H1, W1);
+  if (!rc) rc = wgrad(n, 1, n->in_e2, dy[1], n->g16, H1, W1);
   if (!rc) rc = dgrad(n, 1, n->g16, n->gA, H1, W1);                  // d in_e2 (P1 x 32)
   pool2_bwd_add_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gA, n->gE1, H0, W0, 32);
   relu_mask_kernel<<<blocks_for(P0 * 32), 256, 0, s>>>(n->gE1, n->e1, dy[0], n->g16, P0 * 32);
-  wgrad(n, 0, n->x0, dy[0], n->g16, H0, W0);
+  if (!rc) rc = wgrad(n, 0, n->x0, dy[0], n->g16, H0, W0);
   if (rc) return rc;
   NTRY(n, cudaGetLastError());
   if (loss_out) {
@@ -772,6 +694,9 @@ AMH_API int amh_net_read(amh_net* n, int32_t which, float* out, int64_t* count) 
 AMH_API int amh_net_synchronize(amh_net* n) {
   if (!n) return AMH_EINVAL;
   NTRY(n, cudaStreamSynchronize(n->stream));
+  unsigned int st = 0;
+  NTRY(n, cudaMemcpy(&st, n->status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st) return nfail(n, AMH_EDEVICE, "a convolution's barrier wait gave up (status 0x%x)", st);
   return AMH_OK;
 }
 
