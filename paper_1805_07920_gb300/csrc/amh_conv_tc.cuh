@@ -3,20 +3,20 @@
 // FP32 accumulator in tensor memory, BF16 operands brought into shared memory
 // by the tensor memory accelerator (cp.async.bulk.tensor).
 //
-// Implicit GEMM: D (128 pixels x Cout) = sum over the 9 taps t and the input
-// channels ci of X (pixel + off(t), ci) W (t, co, ci).  A CTA owns 128
-// consecutive pixels of one row and every output channel; one K step is one
-// tap and 16 input channels.  Per step, four TMA boxes land in a stage of the
-// shared-memory ring: the activations of the 128 pixels shifted by the tap
-// (two boxes of 8 channels; rows or columns outside the image read as zeros,
-// which is the convolution's padding) and the tap's weights (two boxes of 8
-// channels x Cout).  Each box is 16 bytes per row, so a stage holds both
-// operands in the tensor cores' K-major layout without swizzling: 8 x 16-byte
-// core matrices, 128 bytes apart along M / N, the second 8 channels 2048
-// bytes after the first.  A producer warp keeps the ring full, an MMA warp
-// consumes it and recycles each stage once the MMA that read it has
-// committed, and the epilogue warps read the accumulator with tcgen05.ld and
-// apply bias, ReLU, skip addition and the BF16 / FP32 stores.
+// Implicit GEMM: D (pixels x Cout) = sum over the 9 taps t and the input
+// channels ci of X (pixel + off(t), ci) W (t, co, ci), one MMA per tap and 16
+// input channels (M = 128 pixels of one row, N = a block of output channels,
+// K = 16).  Both operands sit in shared memory in the tensor cores' K-major
+// layout without swizzling: 8 x 16-byte core matrices, rows 16 bytes apart
+// along M / N, planes of 8 channels along K.  The forward / data-gradient
+// kernel keeps its block of weights resident and streams input rows with a
+// one-pixel halo, each row loaded once per run of vertically adjacent tiles
+// (its comment below gives the schedule); the weight-gradient kernel streams
+// pixel chunks of channel-major copies.  A producer warp issues the TMA
+// copies, an MMA warp consumes them and recycles each buffer once the MMAs
+// that read it have committed, and the epilogue warps read the accumulator
+// with tcgen05.ld and apply bias, ReLU, skip addition and the BF16 / FP32
+// stores.
 //
 // Layout: activations (H, W, C) BF16 with C a multiple of 16; weights (9,
 // Cout, Cin) BF16, tap t = 3 (dy + 1) + (dx + 1); Cout a multiple of 16, at
@@ -43,16 +43,6 @@ struct alignas(1024) Stage {
   uint8_t b[2][kMaxCout * 16];
 };
 constexpr size_t kSmemBytes = kStages * sizeof(Stage) + 1024;   // + alignment slack
-
-struct ConvTcArgs {
-  const float* bias;          // Cout or null
-  const __nv_bfloat16* skip;  // (H, W, Cout) added after the ReLU, or null
-  __nv_bfloat16* y16;         // (H, W, Cout) BF16 output (after ReLU + skip), or null
-  __nv_bfloat16* r16;         // (H, W, Cout) ReLU output before the skip, or null
-  float* y32;                 // (H, W, Cout) FP32 output, or null
-  unsigned int* status;       // bit 0: a barrier wait gave up
-  int H, W, Cin, Cout, relu;
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -82,13 +72,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
-// shared-memory matrix descriptor, K-major, no swizzle: start address,
-// leading byte offset (between the two 8-element core matrices along K),
-// stride byte offset (between 8-row groups along M / N), descriptor version 1
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor, K-major: start address, leading byte
+// offset (without swizzling: between the two 8-element core matrices along
+// K), stride byte offset (between 8-row groups along M / N), descriptor
+// version 1, base offset 0 and the layout type in bits 61-63 (0: no swizzle;
+// 2, 4, 6: rows of 128, 64, 32 bytes with the matching swizzle, whose pattern
+// follows the shared-memory address bits, so a start moved by whole rows
+// stays consistent with what the TMA wrote)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7u) << 61);
 }
+__host__ __device__ constexpr uint32_t swizzle_layout(int pitch) { return pitch == 128 ? 2u : pitch == 64 ? 4u : 6u; }
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24
 __host__ __device__ constexpr uint32_t mma_idesc(int m, int n) {
@@ -107,27 +102,103 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 // Persistent, warp-specialised: warps 0-3 drain the accumulator (warp w owns
 // TMEM lanes 32 w .. 32 w + 31, i.e. pixels 32 w .. 32 w + 31 of the tile),
-// warp 4 produces (TMA into the ring), warp 5 allocates the tensor memory and
-// issues the MMAs.  Two accumulators in tensor memory let the epilogue of one
-// tile overlap the MMAs of the next.  The CTA walks the tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...; tile = (row y, 128-pixel segment).
+// warp 4 produces (TMA), warp 5 allocates the tensor memory and issues the
+// MMAs.  Two accumulators in tensor memory let the epilogue of one tile
+// overlap the MMAs of the next.
 constexpr int kThreads = 192;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tx,
-                                                              const __grid_constant__ CUtensorMap tw,
+// Forward / data-gradient kernel.  A tile is 128 consecutive pixels of one
+// output row and one block of Nb output channels; CTA (bx, by) owns channel
+// block by and a contiguous range of the tiles ordered (128-pixel column
+// segment, row), i.e. runs of vertically adjacent tiles.  Its Nb x Cin x 9
+// weights are loaded into shared memory once.  The input enters as slabs:
+// one input row, 130 pixels (the tile's 128 and one halo pixel on each side)
+// x all Cin channels.  Channels are split into blocks of 64 (128-byte rows)
+// and a tail of 16 or 32 (32- or 64-byte rows); each block is one TMA box
+// with the swizzle of its row length, 1024-byte aligned, and the weights of
+// a tap use the same blocks.  Output row y reads the slabs of input rows
+// y - 1, y, y + 1, and the tap (dx, dy) of slab y + dy is the same block seen
+// from row 1 + dx: its matrix descriptor starts 1 + dx rows later (the
+// swizzle pattern follows the address, so the shifted view reads what the
+// TMA wrote).  So each input row of a run is loaded once and feeds
+// 9 Cin / 16 MMAs (M = 128, N = Nb, K = 16) for three output rows.  The slabs
+// sit in a ring of S stages; slab k is released when output row k + 1 (the
+// last one reading it) has committed its MMAs.
+constexpr int kHalo = kM + 2;               // pixels per slab row
+constexpr int kMaxStages = 8;
+constexpr int kSkipAhead = 64;             // skip channels an epilogue lane fetches before its tile is ready
+
+struct ConvTcArgs {
+  const float* bias;          // Cout or null
+  const __nv_bfloat16* skip;  // (H, W, Cout) added after the ReLU, or null
+  __nv_bfloat16* y16;         // (H, W, Cout) BF16 output (after ReLU + skip), or null
+  __nv_bfloat16* r16;         // (H, W, Cout) ReLU output before the skip, or null
+  float* y32;                 // (H, W, Cout) FP32 output, or null
+  unsigned int* status;       // bit 0: a barrier wait gave up
+  int H, W, Cin, Cout, relu;
+  int Nb;                     // output channels per CTA (a multiple of 16 dividing Cout)
+  int S;                      // slab stages (3 .. kMaxStages)
+};
+
+// channel blocks of a Cin-channel operand: cin / 64 blocks of 64 channels,
+// then a tail of cin % 64 (0, 16 or 32) channels; each block's region is
+// rows x (2 x its channels) bytes rounded up to 1 KB
+__host__ __device__ constexpr size_t round_1k(size_t b) { return (b + 1023) & ~(size_t)1023; }
+__host__ __device__ constexpr size_t conv_block_bytes(int cin, int rows) {
+  return (size_t)(cin / 64) * round_1k((size_t)rows * 128) + (cin % 64 ? round_1k((size_t)rows * 2 * (cin % 64)) : 0);
+}
+// dynamic shared memory of conv3x3_tc_kernel: alignment slack, the weights
+// (9 taps of Nb rows), the slab ring (rows of kHalo pixels)
+__host__ __device__ constexpr size_t conv_wtap_bytes(int cin, int nb) { return conv_block_bytes(cin, nb); }
+__host__ __device__ constexpr size_t conv_weight_bytes(int cin, int nb) { return 9 * conv_wtap_bytes(cin, nb); }
+__host__ __device__ constexpr size_t conv_slab_bytes(int cin) { return conv_block_bytes(cin, kHalo); }
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin, int nb, int s) {
+  return 1024 + conv_weight_bytes(cin, nb) + (size_t)s * conv_slab_bytes(cin);
+}
+// tensor-memory columns of one accumulator (allocations are powers of two >= 32)
+__host__ __device__ constexpr uint32_t conv_acc_cols(int nb) { return nb <= 32 ? 32u : nb <= 64 ? 64u : 128u; }
+
+// run r of the CTA's tile range: tiles u .. u + len - 1 of one column segment
+struct TileRun {
+  int seg, y0, len;
+};
+__device__ __forceinline__ bool next_run(int& u, int hi, int H, TileRun& r) {
+  if (u >= hi) return false;
+  r.seg = u / H;
+  r.y0 = u % H;
+  r.len = min(hi - u, H - r.y0);
+  u += r.len;
+  return true;
+}
+
+// tx_main / tw_main: boxes of 64 channels x (kHalo pixels | Nb output
+// channels), 128-byte swizzle; tx_tail / tw_tail: the same for the tail
+// channels (unused when Cin is a multiple of 64)
+__global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tx_main,
+                                                              const __grid_constant__ CUtensorMap tx_tail,
+                                                              const __grid_constant__ CUtensorMap tw_main,
+                                                              const __grid_constant__ CUtensorMap tw_tail,
                                                               const ConvTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  Stage* st = reinterpret_cast<Stage*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
+  uint8_t* wsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = a.S, Nb = a.Nb, nmain = a.Cin / 64, tail = a.Cin % 64, nblk = nmain + (tail ? 1 : 0);
+  uint8_t* slabs = wsm + conv_weight_bytes(a.Cin, Nb);
+  const uint32_t slab_bytes = (uint32_t)conv_slab_bytes(a.Cin), wtap_bytes = (uint32_t)conv_wtap_bytes(a.Cin, Nb);
+  // per channel block: byte offset in a slab / a tap's weights
+  const uint32_t sblk = (uint32_t)round_1k((size_t)kHalo * 128), wblk = (uint32_t)round_1k((size_t)Nb * 128);
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2], wbar;
   __shared__ uint32_t tmem_slot;
+  __shared__ float bias_s[kMaxCout];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nc = a.Cin / 16, nk = 9 * nc;
+  const int co0 = blockIdx.y * Nb;
   const int nseg = (a.W + kM - 1) / kM, ntiles = a.H * nseg;
-  const uint32_t ncols = a.Cout <= 32 ? 32u : a.Cout <= 64 ? 64u : 128u;   // one accumulator
+  const int lo = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
+  const int hi = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x);
+  const uint32_t ncols = conv_acc_cols(Nb);
 
   if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -135,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < kStages; s++) {
+    for (int s = 0; s < S; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -143,8 +214,10 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 4);    // one arrival per epilogue warp
     }
+    mbar_init(&wbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int c = tid; c < Nb; c += kThreads) bias_s[c] = a.bias ? a.bias[co0 + c] : 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -152,97 +225,147 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
   bool ok = true;
 
   if (warp == 4) {
-    // producer: a stage is refilled once the MMA that read it has committed
+    // producer: the weights once, then the slabs of every run in order
     if (lane == 0) {
-      const uint32_t bytes = 2u * kM * 16u + 2u * (uint32_t)a.Cout * 16u;
-      uint32_t g = 0;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int y = tile / nseg, x0 = (tile % nseg) * kM;
-        for (int k = 0; k < nk && ok; k++, g++) {
-          const int s = (int)(g % kStages);
-          if (!(ok = mbar_wait(&empty[s], ((g / kStages) & 1u) ^ 1u))) break;
-          const int t = k / nc, ci0 = (k % nc) * 16, dy = t / 3 - 1, dx = t % 3 - 1;
-          mbar_expect_tx(&full[s], bytes);
-#pragma unroll
-          for (int h = 0; h < 2; h++) {
-            tma_load_3d(st[s].a[h], &tx, ci0 + 8 * h, x0 + dx, y + dy, &full[s]);
-            tma_load_3d(st[s].b[h], &tw, ci0 + 8 * h, 0, t, &full[s]);
-          }
+      mbar_expect_tx(&wbar, 9u * (uint32_t)Nb * 2u * (uint32_t)a.Cin);
+      for (int t = 0; t < 9; t++)
+        for (int bk = 0; bk < nblk; bk++)
+          tma_load_3d(wsm + (size_t)t * wtap_bytes + (size_t)bk * wblk, bk < nmain ? &tw_main : &tw_tail, 64 * bk, co0, t,
+                      &wbar);
+      uint32_t gs = 0;
+      TileRun r;
+      for (int u = lo; ok && next_run(u, hi, a.H, r);) {
+        const int x0 = r.seg * kM;
+        for (int k = 0; k < r.len + 2 && ok; k++, gs++) {
+          const uint32_t s = gs % (uint32_t)S;
+          if (!(ok = mbar_wait(&empty[s], ((gs / (uint32_t)S) & 1u) ^ 1u))) break;
+          mbar_expect_tx(&full[s], (uint32_t)kHalo * 2u * (uint32_t)a.Cin);
+          for (int bk = 0; bk < nblk; bk++)
+            tma_load_3d(slabs + (size_t)s * slab_bytes + (size_t)bk * sblk, bk < nmain ? &tx_main : &tx_tail, 64 * bk,
+                        x0 - 1, r.y0 - 1 + k, &full[s]);
         }
       }
     }
   } else if (warp == 5) {
-    // MMA issuer: K steps of a tile accumulate in buffer i % 2
+    // MMA issuer: output row i of a run accumulates 9 Cin / 16 MMAs over the
+    // slabs i, i + 1, i + 2 of the run into accumulator buffer (tile count % 2)
     if (lane == 0) {
-      const uint32_t idesc = mma_idesc(kM, a.Cout);
-      uint32_t g = 0, i = 0;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, i++) {
-        const uint32_t b = i & 1u;
-        if (!(ok = mbar_wait(&acc_empty[b], ((i >> 1) & 1u) ^ 1u))) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + b * ncols;
-        for (int k = 0; k < nk; k++, g++) {
-          const int s = (int)(g % kStages);
-          if (!(ok = mbar_wait(&full[s], (g / kStages) & 1u))) break;
+      const uint32_t idesc = mma_idesc(kM, Nb);
+      const uint32_t wbase = smem_u32(wsm), sbase = smem_u32(slabs);
+      ok = mbar_wait(&wbar, 0);
+      uint32_t gs = 0, tc = 0;
+      TileRun r;
+      for (int u = lo; ok && next_run(u, hi, a.H, r);) {
+        const uint32_t base = gs;
+        for (int i = 0; i < r.len && ok; i++, tc++) {
+          const uint32_t b = tc & 1u;
+          if (!(ok = mbar_wait(&acc_empty[b], ((tc >> 1) & 1u) ^ 1u))) break;
+          for (int j = i == 0 ? 0 : 2; j < 3 && ok; j++) {
+            const uint32_t k = base + (uint32_t)(i + j);
+            ok = mbar_wait(&full[k % (uint32_t)S], (k / (uint32_t)S) & 1u);
+          }
+          if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          mma_bf16(d, smem_desc(smem_u32(st[s].a[0]), kM * 16, 128), smem_desc(smem_u32(st[s].b[0]), kMaxCout * 16, 128),
-                   idesc, k > 0 ? 1u : 0u);
-          mma_commit(&empty[s]);
+          const uint32_t d = tmem + b * ncols;
+          uint32_t acc = 0;
+          for (int dy = 0; dy < 3; dy++) {
+            const uint32_t sa = sbase + ((base + (uint32_t)(i + dy)) % (uint32_t)S) * slab_bytes;
+            for (int bk = 0; bk < nblk; bk++) {
+              const uint32_t pitch = bk < nmain ? 128u : 2u * (uint32_t)tail, lay = swizzle_layout((int)pitch);
+              for (int c = 0; c < (int)pitch / 32; c++) {
+#pragma unroll
+                for (int dx = 0; dx < 3; dx++) {
+                  const uint32_t xa = sa + (uint32_t)bk * sblk + (uint32_t)dx * pitch + 32u * c;
+                  const uint32_t wa = wbase + (uint32_t)(3 * dy + dx) * wtap_bytes + (uint32_t)bk * wblk + 32u * c;
+                  mma_bf16(d, smem_desc(xa, 16, 8 * pitch, lay), smem_desc(wa, 16, 8 * pitch, lay), idesc, acc);
+                  acc = 1;
+                }
+              }
+            }
+          }
+          mma_commit(&acc_full[b]);
+          mma_commit(&empty[(base + (uint32_t)i) % (uint32_t)S]);    // slab i is read by no later row
         }
-        if (ok) mma_commit(&acc_full[b]);
+        if (!ok) break;
+        // the run's last two slabs
+        mma_commit(&empty[(base + (uint32_t)r.len) % (uint32_t)S]);
+        mma_commit(&empty[(base + (uint32_t)r.len + 1) % (uint32_t)S]);
+        gs = base + (uint32_t)r.len + 2;
       }
     }
   } else {
     // epilogue: warp w drains TMEM lanes 32 w .. 32 w + 31 of each tile
-    uint32_t i = 0;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, i++) {
-      const uint32_t b = i & 1u;
-      if (!(ok = mbar_wait(&acc_full[b], (i >> 1) & 1u))) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int y = tile / nseg, x0 = (tile % nseg) * kM;
-      const int r = warp * 32 + lane, px = x0 + r;
-      const size_t o0 = ((size_t)y * a.W + px) * a.Cout;
-      for (int c0 = 0; c0 < a.Cout; c0 += 8) {
-        uint32_t v[8];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-            : "r"(tmem + b * ncols + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (px >= a.W) continue;
-        const size_t o = o0 + c0;
-        float f[8];
+    uint32_t tc = 0;
+    TileRun r;
+    for (int u = lo; ok && next_run(u, hi, a.H, r);) {
+      for (int i = 0; i < r.len && ok; i++, tc++) {
+        const uint32_t b = tc & 1u;
+        const int y = r.y0 + i, px = r.seg * kM + warp * 32 + lane;
+        const bool in = px < a.W;
+        const size_t o0 = ((size_t)y * a.W + (in ? px : 0)) * a.Cout + co0;
+        // the skip values of this lane's pixel (up to kSkipAhead channels),
+        // fetched while the tile's MMAs run
+        uint4 sk[kSkipAhead / 8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-          const float val = __uint_as_float(v[e]) + (a.bias ? a.bias[c0 + e] : 0.f);
-          f[e] = a.relu ? fmaxf(val, 0.f) : val;
-        }
-        __align__(16) __nv_bfloat16 hb[8];
-        if (a.r16) {
+        for (int q = 0; q < kSkipAhead / 8; q++)
+          if (a.skip && in && 8 * q < Nb) sk[q] = __ldg(reinterpret_cast<const uint4*>(a.skip + o0) + q);
+        if (!(ok = mbar_wait(&acc_full[b], (tc >> 1) & 1u))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-          for (int e = 0; e < 8; e++) hb[e] = __float2bfloat16(f[e]);
-          *reinterpret_cast<uint4*>(a.r16 + o) = *reinterpret_cast<const uint4*>(hb);
-        }
-        if (a.skip) {
-          __align__(16) __nv_bfloat16 sk[8];
-          *reinterpret_cast<uint4*>(sk) = *reinterpret_cast<const uint4*>(a.skip + o);
+        for (int c0 = 0; c0 < kMaxCout; c0 += 16) {
+          if (c0 >= Nb) break;
+          uint32_t v[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(tmem + b * ncols + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (!in) continue;
+          const size_t o = o0 + c0;
+          float f[16];
 #pragma unroll
-          for (int e = 0; e < 8; e++) f[e] = __bfloat162float(__float2bfloat16(f[e])) + __bfloat162float(sk[e]);
-        }
-        if (a.y16) {
+          for (int e = 0; e < 16; e++) {
+            const float val = __uint_as_float(v[e]) + bias_s[c0 + e];
+            f[e] = a.relu ? fmaxf(val, 0.f) : val;
+          }
+          __align__(16) __nv_bfloat16 hb[16];
+          if (a.r16) {
 #pragma unroll
-          for (int e = 0; e < 8; e++) hb[e] = __float2bfloat16(f[e]);
-          *reinterpret_cast<uint4*>(a.y16 + o) = *reinterpret_cast<const uint4*>(hb);
+            for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
+            reinterpret_cast<uint4*>(a.r16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
+            reinterpret_cast<uint4*>(a.r16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+          }
+          if (a.skip) {
+            __align__(16) __nv_bfloat16 skb[16];
+            if (c0 < kSkipAhead) {
+              reinterpret_cast<uint4*>(skb)[0] = sk[c0 / 8];
+              reinterpret_cast<uint4*>(skb)[1] = sk[c0 / 8 + 1];
+            } else {
+              reinterpret_cast<uint4*>(skb)[0] = __ldg(reinterpret_cast<const uint4*>(a.skip + o));
+              reinterpret_cast<uint4*>(skb)[1] = __ldg(reinterpret_cast<const uint4*>(a.skip + o) + 1);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; e++) f[e] = __bfloat162float(__float2bfloat16(f[e])) + __bfloat162float(skb[e]);
+          }
+          if (a.y16) {
+#pragma unroll
+            for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
+            reinterpret_cast<uint4*>(a.y16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
+            reinterpret_cast<uint4*>(a.y16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+          }
+          if (a.y32) {
+            float4* q = reinterpret_cast<float4*>(a.y32 + o);
+#pragma unroll
+            for (int e = 0; e < 4; e++) q[e] = make_float4(f[4 * e], f[4 * e + 1], f[4 * e + 2], f[4 * e + 3]);
+          }
         }
-        if (a.y32) {
-          reinterpret_cast<float4*>(a.y32 + o)[0] = make_float4(f[0], f[1], f[2], f[3]);
-          reinterpret_cast<float4*>(a.y32 + o)[1] = make_float4(f[4], f[5], f[6], f[7]);
-        }
+        // this warp's lanes of buffer b may be overwritten by the next tile's MMAs
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
       }
-      // this warp's lanes of buffer b may be overwritten by the next tile's MMAs
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
   }
   if (!ok && (lane == 0)) atomicOr(a.status, 1u);
@@ -391,12 +514,35 @@ __global__ void __launch_bounds__(256) to_channel_major_kernel(const __nv_bfloat
   }
 }
 
-// CTAs of conv3x3_tc_kernel that fit on one SM: the shared-memory ring and
-// the tensor memory (512 columns, two accumulators per CTA) both bound it
-__host__ __device__ constexpr int ctas_per_sm(int cout) {
-  const int cols = 2 * (cout <= 32 ? 32 : cout <= 64 ? 64 : 128);
-  const int by_tmem = 512 / cols, by_smem = (int)((228u * 1024u) / (kSmemBytes + 1024u));
-  return by_tmem < by_smem ? by_tmem : by_smem;
+// Launch plan of conv3x3_tc_kernel for one layer: the largest channel block
+// Nb (a multiple of 16 dividing Cout) whose weights and four slabs fit in
+// 220 KB of shared memory; then as many slab stages (at most kMaxStages) as
+// fit in 110 KB, so that two CTAs share an SM, or else in 220 KB; and the
+// CTAs that fit on one SM by shared memory and by tensor memory (512
+// columns, two accumulators per CTA).
+struct ConvPlan {
+  int Nb, S, ctas_per_sm;
+  size_t smem;
+};
+constexpr size_t kConvSmemCap = 220 * 1024;   // dynamic; the kernel's static shared memory comes on top
+inline ConvPlan conv_plan(int cin, int cout) {
+  const size_t cap = kConvSmemCap, half = kConvSmemCap / 2, slab = conv_slab_bytes(cin);
+  int nb = 16;
+  for (int d = 1; d <= cout / 16; d++) {
+    if (cout % d || (cout / d) % 16) continue;
+    if (conv_smem_bytes(cin, cout / d, 4) <= cap) {
+      nb = cout / d;
+      break;
+    }
+  }
+  const size_t budget = conv_smem_bytes(cin, nb, 4) <= half ? half : cap;
+  int s = (int)((budget - conv_smem_bytes(cin, nb, 0)) / slab);
+  s = s < kMaxStages ? s : kMaxStages;
+  ConvPlan p{nb, s, 1, conv_smem_bytes(cin, nb, s)};
+  const int by_tmem = 512 / (int)(2 * conv_acc_cols(nb)), by_smem = (int)((228 * 1024) / (p.smem + 2048));   // + reserved and static
+  p.ctas_per_sm = by_tmem < by_smem ? by_tmem : by_smem;
+  if (p.ctas_per_sm < 1) p.ctas_per_sm = 1;
+  return p;
 }
 
 }  // namespace tc

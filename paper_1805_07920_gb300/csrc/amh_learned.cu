@@ -309,7 +309,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // pitch0 elements (>= d0), read in boxes of (b0, b1, b2); reads outside the
 // tensor return zeros
 bool bf16_map(CUtensorMap* m, const void* p, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
-              uint32_t b2 = 1, uint64_t pitch0 = 0) {
+              uint32_t b2 = 1, uint64_t pitch0 = 0, CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   if (!pitch0) pitch0 = d0;
@@ -318,32 +318,62 @@ bool bf16_map(CUtensorMap* m, const void* p, uint64_t d0, uint64_t d1, uint64_t 
   cuuint32_t box[3] = {b0, b1, b2};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(p), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+// the swizzle of a channel block of conv3x3_tc_kernel: rows of 2 x nch bytes
+CUtensorMapSwizzle block_swizzle(int nch) {
+  return nch == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : nch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
 }
 
 // 3x3 convolution on the tensor cores (amh_conv_tc.cuh): x (H, W, Cin), w (9,
 // Cout, Cin), Cin and Cout multiples of 16, Cout at most 128
 int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* skip,
          __nv_bfloat16* y16, __nv_bfloat16* r16, float* y32, int H, int W, int Cin, int Cout, int relu) {
-  if (Cin % 16 || Cout % 16 || Cout > tc::kMaxCout) return nfail(n, AMH_EINVAL, "conv: channel counts");
-  CUtensorMap mx, mw;
-  if (!bf16_map(&mx, x, Cin, W, H, 8, tc::kM) || !bf16_map(&mw, w, Cin, Cout, 9, 8, Cout))
-    return nfail(n, AMH_ECUDA, "conv: tensor map encoding failed");
-  const tc::ConvTcArgs a{bias, skip, y16, r16, y32, n->status, H, W, Cin, Cout, relu};
-  // persistent grid: as many CTAs as fit on the SMs at once (every CTA holds
-  // its tensor memory until it exits), at most one per tile
+  if (Cin % 16 || Cin > 128 || Cin % 64 == 48 || Cout % 16 || Cout > tc::kMaxCout)
+    return nfail(n, AMH_EINVAL, "conv: channel counts");
+  const tc::ConvPlan p = tc::conv_plan(Cin, Cout);
+  // one map per kind of channel block (64 channels; the 16 or 32 of the
+  // tail); a kind the layer lacks gets a copy of the other
+  CUtensorMap mx[2], mw[2];
+  const int tail = Cin % 64;
+  bool ok = true;
+  if (Cin >= 64)
+    ok = bf16_map(&mx[0], x, Cin, W, H, 64, tc::kHalo, 1, 0, block_swizzle(64)) &&
+         bf16_map(&mw[0], w, Cin, Cout, 9, 64, p.Nb, 1, 0, block_swizzle(64));
+  if (ok && tail)
+    ok = bf16_map(&mx[1], x, Cin, W, H, tail, tc::kHalo, 1, 0, block_swizzle(tail)) &&
+         bf16_map(&mw[1], w, Cin, Cout, 9, tail, p.Nb, 1, 0, block_swizzle(tail));
+  if (!ok) return nfail(n, AMH_ECUDA, "conv: tensor map encoding failed");
+  if (Cin < 64) mx[0] = mx[1], mw[0] = mw[1];
+  if (!tail) mx[1] = mx[0], mw[1] = mw[0];
+  const tc::ConvTcArgs a{bias, skip, y16, r16, y32, n->status, H, W, Cin, Cout, relu, p.Nb, p.S};
+  // persistent grid: per channel block, as many CTAs as fit on the SMs at
+  // once (every CTA holds its tensor memory until it exits), at most one per
+  // tile
   static int n_sm[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!n_sm[dev & 63]) cudaDeviceGetAttribute(&n_sm[dev & 63], cudaDevAttrMultiProcessorCount, dev);
   static std::once_flag once[64];
-  std::call_once(once[dev & 63], [] {
-    cudaFuncSetAttribute(tc::conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes);
+  static cudaError_t attr_err[64] = {};
+  static int regs[64] = {};
+  std::call_once(once[dev & 63], [dev] {
+    attr_err[dev & 63] = cudaFuncSetAttribute(tc::conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)tc::kConvSmemCap);
+    cudaFuncAttributes fa;
+    if (attr_err[dev & 63] == cudaSuccess) attr_err[dev & 63] = cudaFuncGetAttributes(&fa, tc::conv3x3_tc_kernel);
+    if (attr_err[dev & 63] == cudaSuccess) regs[dev & 63] = fa.numRegs;
   });
-  const int ntiles = H * ((W + tc::kM - 1) / tc::kM);
-  const int grid = std::max(1, std::min(ntiles, n_sm[dev & 63] * tc::ctas_per_sm(Cout)));
-  tc::conv3x3_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, n->stream>>>(mx, mw, a);
+  if (attr_err[dev & 63] != cudaSuccess)
+    return nfail(n, AMH_ECUDA, "conv: shared-memory attribute: %s", cudaGetErrorString(attr_err[dev & 63]));
+  if (p.smem > tc::kConvSmemCap) return nfail(n, AMH_EINVAL, "conv: shared memory plan too large");
+  // CTAs resident per SM: the plan's, and what the register file holds
+  const int by_regs = 65536 / (((regs[dev & 63] + 7) & ~7) * tc::kThreads);
+  const int cps = std::max(1, std::min(p.ctas_per_sm, by_regs));
+  const int nblk = Cout / p.Nb, ntiles = H * ((W + tc::kM - 1) / tc::kM);
+  const int gx = std::max(1, std::min(ntiles, n_sm[dev & 63] * cps / nblk));
+  tc::conv3x3_tc_kernel<<<dim3(gx, nblk), tc::kThreads, p.smem, n->stream>>>(mx[0], mx[1], mw[0], mw[1], a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
   return AMH_OK;
