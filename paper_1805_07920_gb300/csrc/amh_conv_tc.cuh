@@ -53,15 +53,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 // true once the barrier's phase with the given parity has completed; false
-// after kWaitTries unsuccessful tries
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+// after kWaitTries unsuccessful tries.  A waiter that is not on the critical
+// path passes sleep_ns, so that between tries it leaves the issue slots of its
+// SM sub-partition to the warps that are.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t sleep_ns = 0) {
   uint32_t done = 0;
-  for (uint32_t it = 0; it < kWaitTries && !done; it++) {
+  for (uint32_t it = 0; it < kWaitTries; it++) {
     asm volatile(
         "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(done)
         : "r"(smem_u32(b)), "r"(parity)
         : "memory");
+    if (done) break;
+    if (sleep_ns) __nanosleep(sleep_ns);
   }
   return done != 0;
 }
@@ -84,6 +88,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7u) << 61);
 }
 __host__ __device__ constexpr uint32_t swizzle_layout(int pitch) { return pitch == 128 ? 2u : pitch == 64 ? 4u : 6u; }
+// the same descriptor as two 32-bit words: the low one (start >> 4, leading
+// byte offset 16) moves with the operand, the high one (stride 8 rows of
+// `pitch` bytes, version, swizzle) is fixed per channel block
+__device__ __forceinline__ uint32_t desc_lo(uint32_t addr) { return ((addr >> 4) & 0x3FFFu) | (1u << 16); }
+__device__ __forceinline__ uint32_t desc_hi(uint32_t pitch) {
+  return ((8u * pitch) >> 4) | (1u << 14) | (swizzle_layout((int)pitch) << 29);
+}
+__device__ __forceinline__ uint64_t desc_pack(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
+
+// position in a ring of S buffers: the slot and the parity of its current use
+struct RingPos {
+  uint32_t slot, phase;
+  __device__ __forceinline__ RingPos next(uint32_t S) const {
+    return slot + 1 == S ? RingPos{0u, phase ^ 1u} : RingPos{slot + 1, phase};
+  }
+};
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24
 __host__ __device__ constexpr uint32_t mma_idesc(int m, int n) {
@@ -232,17 +252,17 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
         for (int bk = 0; bk < nblk; bk++)
           tma_load_3d(wsm + (size_t)t * wtap_bytes + (size_t)bk * wblk, bk < nmain ? &tw_main : &tw_tail, 64 * bk, co0, t,
                       &wbar);
-      uint32_t gs = 0;
+      RingPos q{0u, 0u};
       TileRun r;
       for (int u = lo; ok && next_run(u, hi, a.H, r);) {
         const int x0 = r.seg * kM;
-        for (int k = 0; k < r.len + 2 && ok; k++, gs++) {
-          const uint32_t s = gs % (uint32_t)S;
-          if (!(ok = mbar_wait(&empty[s], ((gs / (uint32_t)S) & 1u) ^ 1u))) break;
-          mbar_expect_tx(&full[s], (uint32_t)kHalo * 2u * (uint32_t)a.Cin);
+        for (int k = 0; k < r.len + 2 && ok; k++, q = q.next((uint32_t)S)) {
+          if (!(ok = mbar_wait(&empty[q.slot], q.phase ^ 1u))) break;
+          mbar_expect_tx(&full[q.slot], (uint32_t)kHalo * 2u * (uint32_t)a.Cin);
+          uint8_t* dst = slabs + (size_t)q.slot * slab_bytes;
           for (int bk = 0; bk < nblk; bk++)
-            tma_load_3d(slabs + (size_t)s * slab_bytes + (size_t)bk * sblk, bk < nmain ? &tx_main : &tx_tail, 64 * bk,
-                        x0 - 1, r.y0 - 1 + k, &full[s]);
+            tma_load_3d(dst + (size_t)bk * sblk, bk < nmain ? &tx_main : &tx_tail, 64 * bk, x0 - 1, r.y0 - 1 + k,
+                        &full[q.slot]);
         }
       }
     }
@@ -251,46 +271,61 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
     // slabs i, i + 1, i + 2 of the run into accumulator buffer (tile count % 2)
     if (lane == 0) {
       const uint32_t idesc = mma_idesc(kM, Nb);
-      const uint32_t wbase = smem_u32(wsm), sbase = smem_u32(slabs);
+      const uint32_t hi_main = desc_hi(128u), hi_tail = desc_hi(2u * (uint32_t)tail);
+      const uint32_t w_lo = desc_lo(smem_u32(wsm)), s_lo = desc_lo(smem_u32(slabs));
+      const uint32_t wtap16 = wtap_bytes >> 4, slab16 = slab_bytes >> 4, sblk16 = sblk >> 4, wblk16 = wblk >> 4;
+      const uint32_t tail16 = (2u * (uint32_t)tail) >> 4;      // the tail's row pitch, in 16-byte units
       ok = mbar_wait(&wbar, 0);
-      uint32_t gs = 0, tc = 0;
+      uint32_t tc = 0;
+      RingPos q{0u, 0u};    // ring position of the next slab
       TileRun r;
       for (int u = lo; ok && next_run(u, hi, a.H, r);) {
-        const uint32_t base = gs;
+        RingPos q0 = q, q1 = q.next((uint32_t)S);    // slabs i and i + 1 of the run
         for (int i = 0; i < r.len && ok; i++, tc++) {
           const uint32_t b = tc & 1u;
+          const RingPos q2 = q1.next((uint32_t)S);
           if (!(ok = mbar_wait(&acc_empty[b], ((tc >> 1) & 1u) ^ 1u))) break;
-          for (int j = i == 0 ? 0 : 2; j < 3 && ok; j++) {
-            const uint32_t k = base + (uint32_t)(i + j);
-            ok = mbar_wait(&full[k % (uint32_t)S], (k / (uint32_t)S) & 1u);
-          }
-          if (!ok) break;
+          if (i == 0) ok = mbar_wait(&full[q0.slot], q0.phase) && mbar_wait(&full[q1.slot], q1.phase);
+          if (!(ok = ok && mbar_wait(&full[q2.slot], q2.phase))) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + b * ncols;
           uint32_t acc = 0;
+#pragma unroll
           for (int dy = 0; dy < 3; dy++) {
-            const uint32_t sa = sbase + ((base + (uint32_t)(i + dy)) % (uint32_t)S) * slab_bytes;
-            for (int bk = 0; bk < nblk; bk++) {
-              const uint32_t pitch = bk < nmain ? 128u : 2u * (uint32_t)tail, lay = swizzle_layout((int)pitch);
-              for (int c = 0; c < (int)pitch / 32; c++) {
+            const uint32_t slot = dy == 0 ? q0.slot : dy == 1 ? q1.slot : q2.slot;
+            const uint32_t xs = s_lo + slot * slab16, ws = w_lo + (uint32_t)(3 * dy) * wtap16;
+            for (int bk = 0; bk < nmain; bk++) {
+              const uint32_t xb = xs + (uint32_t)bk * sblk16, wb = ws + (uint32_t)bk * wblk16;
+#pragma unroll
+              for (int c = 0; c < 4; c++)
 #pragma unroll
                 for (int dx = 0; dx < 3; dx++) {
-                  const uint32_t xa = sa + (uint32_t)bk * sblk + (uint32_t)dx * pitch + 32u * c;
-                  const uint32_t wa = wbase + (uint32_t)(3 * dy + dx) * wtap_bytes + (uint32_t)bk * wblk + 32u * c;
-                  mma_bf16(d, smem_desc(xa, 16, 8 * pitch, lay), smem_desc(wa, 16, 8 * pitch, lay), idesc, acc);
+                  mma_bf16(d, desc_pack(xb + 8u * dx + 2u * c, hi_main), desc_pack(wb + dx * wtap16 + 2u * c, hi_main),
+                           idesc, acc);
                   acc = 1;
                 }
-              }
+            }
+            if (tail) {
+              const uint32_t xb = xs + (uint32_t)nmain * sblk16, wb = ws + (uint32_t)nmain * wblk16;
+              for (uint32_t c = 0; c < tail16 / 2; c++)
+#pragma unroll
+                for (int dx = 0; dx < 3; dx++) {
+                  mma_bf16(d, desc_pack(xb + tail16 * dx + 2u * c, hi_tail), desc_pack(wb + dx * wtap16 + 2u * c, hi_tail),
+                           idesc, acc);
+                  acc = 1;
+                }
             }
           }
           mma_commit(&acc_full[b]);
-          mma_commit(&empty[(base + (uint32_t)i) % (uint32_t)S]);    // slab i is read by no later row
+          mma_commit(&empty[q0.slot]);    // slab i is read by no later row
+          q0 = q1;
+          q1 = q2;
         }
         if (!ok) break;
         // the run's last two slabs
-        mma_commit(&empty[(base + (uint32_t)r.len) % (uint32_t)S]);
-        mma_commit(&empty[(base + (uint32_t)r.len + 1) % (uint32_t)S]);
-        gs = base + (uint32_t)r.len + 2;
+        mma_commit(&empty[q0.slot]);
+        mma_commit(&empty[q1.slot]);
+        q = q1.next((uint32_t)S);
       }
     }
   } else {
@@ -309,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
 #pragma unroll
         for (int q = 0; q < kSkipAhead / 8; q++)
           if (a.skip && in && 8 * q < Nb) sk[q] = __ldg(reinterpret_cast<const uint4*>(a.skip + o0) + q);
-        if (!(ok = mbar_wait(&acc_full[b], (tc >> 1) & 1u))) break;
+        if (!(ok = mbar_wait(&acc_full[b], (tc >> 1) & 1u, 64))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int c0 = 0; c0 < kMaxCout; c0 += 16) {
