@@ -120,11 +120,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// Persistent, warp-specialised: warps 0-3 drain the accumulator (warp w owns
-// TMEM lanes 32 w .. 32 w + 31, i.e. pixels 32 w .. 32 w + 31 of the tile),
-// warp 4 produces (TMA), warp 5 allocates the tensor memory and issues the
-// MMAs.  Two accumulators in tensor memory let the epilogue of one tile
-// overlap the MMAs of the next.
+// Both kernels are persistent and warp-specialised: epilogue warps drain the
+// accumulator (a warp reads the TMEM lanes of its SM sub-partition, lanes
+// 32 (w % 4) .. 32 (w % 4) + 31), one warp produces (TMA), one allocates the
+// tensor memory and issues the MMAs.  Two accumulators in tensor memory let
+// the epilogue of one tile overlap the MMAs of the next.  The weight-gradient
+// kernel has 4 epilogue warps (kThreads); the convolution kernel has 4 per
+// 16 output channels of its block (conv_threads), so that the chunks of a
+// tile drain in parallel.
 constexpr int kThreads = 192;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
@@ -150,7 +153,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 // last one reading it) has committed its MMAs.
 constexpr int kHalo = kM + 2;               // pixels per slab row
 constexpr int kMaxStages = 8;
-constexpr int kSkipAhead = 64;             // skip channels an epilogue lane fetches before its tile is ready
+constexpr int kConvMaxNb = 64;              // output channels per CTA
+// threads of conv3x3_tc_kernel: 4 epilogue warps per 16 output channels of the
+// block (one per TMEM lane quarter and 16-channel chunk), the producer and the
+// MMA warp
+__host__ __device__ constexpr int conv_threads(int nb) { return 32 * (4 * (nb / 16) + 2); }
+constexpr int kConvMaxThreads = 32 * (4 * (kConvMaxNb / 16) + 2);
 
 struct ConvTcArgs {
   const float* bias;          // Cout or null
@@ -160,7 +168,7 @@ struct ConvTcArgs {
   float* y32;                 // (H, W, Cout) FP32 output, or null
   unsigned int* status;       // bit 0: a barrier wait gave up
   int H, W, Cin, Cout, relu;
-  int Nb;                     // output channels per CTA (a multiple of 16 dividing Cout)
+  int Nb;                     // output channels per CTA (a multiple of 16 dividing Cout, at most kConvMaxNb)
   int S;                      // slab stages (3 .. kMaxStages)
 };
 
@@ -198,7 +206,7 @@ __device__ __forceinline__ bool next_run(int& u, int hi, int H, TileRun& r) {
 // tx_main / tw_main: boxes of 64 channels x (kHalo pixels | Nb output
 // channels), 128-byte swizzle; tx_tail / tw_tail: the same for the tail
 // channels (unused when Cin is a multiple of 64)
-__global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tx_main,
+__global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tx_main,
                                                               const __grid_constant__ CUtensorMap tx_tail,
                                                               const __grid_constant__ CUtensorMap tw_main,
                                                               const __grid_constant__ CUtensorMap tw_tail,
@@ -214,13 +222,14 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
   __shared__ uint32_t tmem_slot;
   __shared__ float bias_s[kMaxCout];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int w_prod = 4 * (Nb / 16), w_mma = w_prod + 1;
   const int co0 = blockIdx.y * Nb;
   const int nseg = (a.W + kM - 1) / kM, ntiles = a.H * nseg;
   const int lo = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
   const int hi = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x);
   const uint32_t ncols = conv_acc_cols(Nb);
 
-  if (warp == 5) {
+  if (warp == w_mma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(2 * ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -232,19 +241,19 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);    // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], (uint32_t)w_prod);    // one arrival per epilogue warp
     }
     mbar_init(&wbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int c = tid; c < Nb; c += kThreads) bias_s[c] = a.bias ? a.bias[co0 + c] : 0.f;
+  for (int c = tid; c < Nb; c += (int)blockDim.x) bias_s[c] = a.bias ? a.bias[co0 + c] : 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   bool ok = true;
 
-  if (warp == 4) {
+  if (warp == w_prod) {
     // producer: the weights once, then the slabs of every run in order
     if (lane == 0) {
       mbar_expect_tx(&wbar, 9u * (uint32_t)Nb * 2u * (uint32_t)a.Cin);
@@ -266,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == w_mma) {
     // MMA issuer: output row i of a run accumulates 9 Cin / 16 MMAs over the
     // slabs i, i + 1, i + 2 of the run into accumulator buffer (tile count % 2)
     if (lane == 0) {
@@ -329,84 +338,77 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
       }
     }
   } else {
-    // epilogue: warp w drains TMEM lanes 32 w .. 32 w + 31 of each tile
+    // epilogue: warp w drains TMEM lanes (pixels) 32 qw .. 32 qw + 31, qw =
+    // w % 4, of output channels c0 .. c0 + 15, c0 = 16 (w / 4), of each tile
+    const int qw = warp & 3, c0 = 16 * (warp >> 2);
     uint32_t tc = 0;
     TileRun r;
     for (int u = lo; ok && next_run(u, hi, a.H, r);) {
       for (int i = 0; i < r.len && ok; i++, tc++) {
         const uint32_t b = tc & 1u;
-        const int y = r.y0 + i, px = r.seg * kM + warp * 32 + lane;
+        const int y = r.y0 + i, px = r.seg * kM + qw * 32 + lane;
         const bool in = px < a.W;
-        const size_t o0 = ((size_t)y * a.W + (in ? px : 0)) * a.Cout + co0;
-        // the skip values of this lane's pixel (up to kSkipAhead channels),
-        // fetched while the tile's MMAs run
-        uint4 sk[kSkipAhead / 8];
-#pragma unroll
-        for (int q = 0; q < kSkipAhead / 8; q++)
-          if (a.skip && in && 8 * q < Nb) sk[q] = __ldg(reinterpret_cast<const uint4*>(a.skip + o0) + q);
+        const size_t o = ((size_t)y * a.W + (in ? px : 0)) * a.Cout + co0 + c0;
+        // this lane's skip values, fetched while the tile's MMAs run
+        uint4 sk0 = make_uint4(0, 0, 0, 0), sk1 = sk0;
+        if (a.skip && in) {
+          sk0 = __ldg(reinterpret_cast<const uint4*>(a.skip + o));
+          sk1 = __ldg(reinterpret_cast<const uint4*>(a.skip + o) + 1);
+        }
         if (!(ok = mbar_wait(&acc_full[b], (tc >> 1) & 1u, 64))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int c0 = 0; c0 < kMaxCout; c0 += 16) {
-          if (c0 >= Nb) break;
-          uint32_t v[16];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-              "%14, %15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(tmem + b * ncols + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (!in) continue;
-          const size_t o = o0 + c0;
-          float f[16];
-#pragma unroll
-          for (int e = 0; e < 16; e++) {
-            const float val = __uint_as_float(v[e]) + bias_s[c0 + e];
-            f[e] = a.relu ? fmaxf(val, 0.f) : val;
-          }
-          __align__(16) __nv_bfloat16 hb[16];
-          if (a.r16) {
-#pragma unroll
-            for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
-            reinterpret_cast<uint4*>(a.r16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
-            reinterpret_cast<uint4*>(a.r16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
-          }
-          if (a.skip) {
-            __align__(16) __nv_bfloat16 skb[16];
-            if (c0 < kSkipAhead) {
-              reinterpret_cast<uint4*>(skb)[0] = sk[c0 / 8];
-              reinterpret_cast<uint4*>(skb)[1] = sk[c0 / 8 + 1];
-            } else {
-              reinterpret_cast<uint4*>(skb)[0] = __ldg(reinterpret_cast<const uint4*>(a.skip + o));
-              reinterpret_cast<uint4*>(skb)[1] = __ldg(reinterpret_cast<const uint4*>(a.skip + o) + 1);
-            }
-#pragma unroll
-            for (int e = 0; e < 16; e++) f[e] = __bfloat162float(__float2bfloat16(f[e])) + __bfloat162float(skb[e]);
-          }
-          if (a.y16) {
-#pragma unroll
-            for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
-            reinterpret_cast<uint4*>(a.y16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
-            reinterpret_cast<uint4*>(a.y16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
-          }
-          if (a.y32) {
-            float4* q = reinterpret_cast<float4*>(a.y32 + o);
-#pragma unroll
-            for (int e = 0; e < 4; e++) q[e] = make_float4(f[4 * e], f[4 * e + 1], f[4 * e + 2], f[4 * e + 3]);
-          }
-        }
-        // this warp's lanes of buffer b may be overwritten by the next tile's MMAs
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + b * ncols + ((uint32_t)(qw * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // buffer b may be overwritten by the next tile's MMAs once every
+        // epilogue warp has its values
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[b]);
+        if (!in) continue;
+        float f[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+          const float val = __uint_as_float(v[e]) + bias_s[c0 + e];
+          f[e] = a.relu ? fmaxf(val, 0.f) : val;
+        }
+        __align__(16) __nv_bfloat16 hb[16];
+        if (a.r16) {
+#pragma unroll
+          for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
+          reinterpret_cast<uint4*>(a.r16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
+          reinterpret_cast<uint4*>(a.r16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+        }
+        if (a.skip) {
+          __align__(16) __nv_bfloat16 skb[16];
+          reinterpret_cast<uint4*>(skb)[0] = sk0;
+          reinterpret_cast<uint4*>(skb)[1] = sk1;
+#pragma unroll
+          for (int e = 0; e < 16; e++) f[e] = __bfloat162float(__float2bfloat16(f[e])) + __bfloat162float(skb[e]);
+        }
+        if (a.y16) {
+#pragma unroll
+          for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
+          reinterpret_cast<uint4*>(a.y16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
+          reinterpret_cast<uint4*>(a.y16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+        }
+        if (a.y32) {
+          float4* q4 = reinterpret_cast<float4*>(a.y32 + o);
+#pragma unroll
+          for (int e = 0; e < 4; e++) q4[e] = make_float4(f[4 * e], f[4 * e + 1], f[4 * e + 2], f[4 * e + 3]);
+        }
       }
     }
   }
   if (!ok && (lane == 0)) atomicOr(a.status, 1u);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 5) {
+  if (warp == w_mma) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ncols));
   }
@@ -564,7 +566,7 @@ inline ConvPlan conv_plan(int cin, int cout) {
   const size_t cap = kConvSmemCap, half = kConvSmemCap / 2, slab = conv_slab_bytes(cin);
   int nb = 16;
   for (int d = 1; d <= cout / 16; d++) {
-    if (cout % d || (cout / d) % 16) continue;
+    if (cout % d || (cout / d) % 16 || cout / d > kConvMaxNb) continue;
     if (conv_smem_bytes(cin, cout / d, 4) <= cap) {
       nb = cout / d;
       break;

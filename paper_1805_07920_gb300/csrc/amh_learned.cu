@@ -369,11 +369,12 @@ int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float
     return nfail(n, AMH_ECUDA, "conv: shared-memory attribute: %s", cudaGetErrorString(attr_err[dev & 63]));
   if (p.smem > tc::kConvSmemCap) return nfail(n, AMH_EINVAL, "conv: shared memory plan too large");
   // CTAs resident per SM: the plan's, and what the register file holds
-  const int by_regs = 65536 / (((regs[dev & 63] + 7) & ~7) * tc::kThreads);
+  const int threads = tc::conv_threads(p.Nb);
+  const int by_regs = 65536 / (((regs[dev & 63] + 7) & ~7) * threads);
   const int cps = std::max(1, std::min(p.ctas_per_sm, by_regs));
   const int nblk = Cout / p.Nb, ntiles = H * ((W + tc::kM - 1) / tc::kM);
   const int gx = std::max(1, std::min(ntiles, n_sm[dev & 63] * cps / nblk));
-  tc::conv3x3_tc_kernel<<<dim3(gx, nblk), tc::kThreads, p.smem, n->stream>>>(mx[0], mx[1], mw[0], mw[1], a);
+  tc::conv3x3_tc_kernel<<<dim3(gx, nblk), threads, p.smem, n->stream>>>(mx[0], mx[1], mw[0], mw[1], a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
   return AMH_OK;
