@@ -55,8 +55,7 @@ FP32_LANES_PER_SM = 128
 # capture, keyed by the hash of the phase kernel's sources it was taken on
 # and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "6fe7ce9ffa83d6f4/fp32_blend": 271977216.0 + 239131392.0,         # profiles/phase_kernel_large.md
-    "6fe7ce9ffa83d6f4/texture_bilinear": 271100160.0 + 235122432.0,   # profiles/phase_kernel_texture_large.md
+    "e22d8597e0db6b5c/fp32_blend": 213867776.0 + 147174656.0,         # profiles/phase_kernel_large.md
 }
 
 

@@ -22,10 +22,11 @@
 using namespace amh;
 
 namespace amh {
-// depth / normal split of the plane array
-__global__ void split_maps_kernel(const float4* __restrict__ plane, size_t n, float* depth, float* normal3) {
+// depth / normal split of the plane array into row-major maps
+__global__ void split_maps_kernel(const float4* __restrict__ plane, int W, int H, float* depth, float* normal3) {
+  const size_t n = (size_t)W * H;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 p = plane[i];
+    const float4 p = plane[state_index((int)(i % W), (int)(i / W), W)];
     if (depth) depth[i] = p.w;
     if (normal3) { normal3[3 * i] = p.x; normal3[3 * i + 1] = p.y; normal3[3 * i + 2] = p.z; }
   }
@@ -233,12 +234,14 @@ AMH_API int amh_create(amh_ctx** out, const amh_params* p, int32_t n_views, cons
 
   CTRY(dev_alloc((void**)&c->d_ref, np * es));
   CTRY(cudaMemcpyAsync(c->d_ref, images[ref], np * es, kind, c->stream));
-  CTRY(dev_alloc((void**)&c->d_plane, np * sizeof(float4)));
-  CTRY(dev_alloc((void**)&c->d_cost, np * sizeof(float)));
-  CTRY(dev_alloc((void**)&c->d_sel, np * sizeof(uint32_t)));
-  CTRY(dev_alloc((void**)&c->d_vbest, np));
-  CTRY(dev_alloc((void**)&c->d_wmask, np * sizeof(uint32_t)));
-  CTRY(dev_alloc((void**)&c->d_choice, np));
+  // the state, in the kernels' layout (state_index)
+  const size_t ns = state_size(c->W, c->H);
+  CTRY(dev_alloc((void**)&c->d_plane, ns * sizeof(float4)));
+  CTRY(dev_alloc((void**)&c->d_cost, ns * sizeof(float)));
+  CTRY(dev_alloc((void**)&c->d_sel, ns * sizeof(uint32_t)));
+  CTRY(dev_alloc((void**)&c->d_vbest, ns));
+  CTRY(dev_alloc((void**)&c->d_wmask, ns * sizeof(uint32_t)));
+  CTRY(dev_alloc((void**)&c->d_choice, ns));
   CTRY(dev_alloc((void**)&c->d_pairs, 2 * kPairCounters * sizeof(unsigned long long)));
   CTRY(cudaMemsetAsync(c->d_pairs, 0, 2 * kPairCounters * sizeof(unsigned long long), c->stream));
   CTRY(dev_alloc((void**)&c->d_status, sizeof(unsigned int)));
@@ -443,14 +446,14 @@ AMH_API int amh_iterate(amh_ctx* c, int32_t k) {
 AMH_API int amh_get_state(amh_ctx* c, amh_state* o, int32_t mem) {
   if (!c || !o) return AMH_EINVAL;
   if (mem != AMH_MEM_HOST && mem != AMH_MEM_DEVICE) return fail(c, AMH_EINVAL, "bad memory kind");
-  const size_t np = (size_t)c->W * c->H;
-  const cudaMemcpyKind k = mem == AMH_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (o->plane) CUDA_TRY(c, cudaMemcpyAsync(o->plane, c->d_plane, np * sizeof(float4), k, c->stream));
-  if (o->cost) CUDA_TRY(c, cudaMemcpyAsync(o->cost, c->d_cost, np * sizeof(float), k, c->stream));
-  if (o->sel) CUDA_TRY(c, cudaMemcpyAsync(o->sel, c->d_sel, np * sizeof(uint32_t), k, c->stream));
-  if (o->vbest) CUDA_TRY(c, cudaMemcpyAsync(o->vbest, c->d_vbest, np, k, c->stream));
-  if (o->wmask) CUDA_TRY(c, cudaMemcpyAsync(o->wmask, c->d_wmask, np * sizeof(uint32_t), k, c->stream));
-  if (o->choice) CUDA_TRY(c, cudaMemcpyAsync(o->choice, c->d_choice, np, k, c->stream));
+  const bool host = mem == AMH_MEM_HOST;
+  const int W = c->W, H = c->H;
+  if (o->plane) CUDA_TRY(c, export_state_field(c->d_plane, o->plane, W, H, 16, host, c->stream));
+  if (o->cost) CUDA_TRY(c, export_state_field(c->d_cost, o->cost, W, H, 4, host, c->stream));
+  if (o->sel) CUDA_TRY(c, export_state_field(c->d_sel, o->sel, W, H, 4, host, c->stream));
+  if (o->vbest) CUDA_TRY(c, export_state_field(c->d_vbest, o->vbest, W, H, 1, host, c->stream));
+  if (o->wmask) CUDA_TRY(c, export_state_field(c->d_wmask, o->wmask, W, H, 4, host, c->stream));
+  if (o->choice) CUDA_TRY(c, export_state_field(c->d_choice, o->choice, W, H, 1, host, c->stream));
   o->t = c->t;
   if (mem == AMH_MEM_HOST) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return AMH_OK;
@@ -461,20 +464,21 @@ AMH_API int amh_set_state(amh_ctx* c, const amh_state* in, int32_t mem) {
   if (mem != AMH_MEM_HOST && mem != AMH_MEM_DEVICE) return fail(c, AMH_EINVAL, "bad memory kind");
   if (!in->plane) return fail(c, AMH_EINVAL, "plane is required");
   if (in->t < 0) return fail(c, AMH_EINVAL, "t < 0");
-  const size_t np = (size_t)c->W * c->H;
-  const cudaMemcpyKind k = mem == AMH_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_plane, in->plane, np * sizeof(float4), k, c->stream));
-  if (in->cost) CUDA_TRY(c, cudaMemcpyAsync(c->d_cost, in->cost, np * sizeof(float), k, c->stream));
-  if (in->sel) CUDA_TRY(c, cudaMemcpyAsync(c->d_sel, in->sel, np * sizeof(uint32_t), k, c->stream));
-  if (in->vbest) CUDA_TRY(c, cudaMemcpyAsync(c->d_vbest, in->vbest, np, k, c->stream));
-  if (in->wmask) CUDA_TRY(c, cudaMemcpyAsync(c->d_wmask, in->wmask, np * sizeof(uint32_t), k, c->stream));
-  if (in->choice) CUDA_TRY(c, cudaMemcpyAsync(c->d_choice, in->choice, np, k, c->stream));
+  const bool host = mem == AMH_MEM_HOST;
+  const int W = c->W, H = c->H;
+  const size_t ns = state_size(W, H);
+  CUDA_TRY(c, import_state_field(in->plane, c->d_plane, W, H, 16, host, c->stream));
+  if (in->cost) CUDA_TRY(c, import_state_field(in->cost, c->d_cost, W, H, 4, host, c->stream));
+  if (in->sel) CUDA_TRY(c, import_state_field(in->sel, c->d_sel, W, H, 4, host, c->stream));
+  if (in->vbest) CUDA_TRY(c, import_state_field(in->vbest, c->d_vbest, W, H, 1, host, c->stream));
+  if (in->wmask) CUDA_TRY(c, import_state_field(in->wmask, c->d_wmask, W, H, 4, host, c->stream));
+  if (in->choice) CUDA_TRY(c, import_state_field(in->choice, c->d_choice, W, H, 1, host, c->stream));
   if (!c->initialized) {  // fields not given start empty
-    if (!in->cost) CUDA_TRY(c, cudaMemsetAsync(c->d_cost, 0, np * sizeof(float), c->stream));
-    if (!in->sel) CUDA_TRY(c, cudaMemsetAsync(c->d_sel, 0, np * sizeof(uint32_t), c->stream));
-    if (!in->vbest) CUDA_TRY(c, cudaMemsetAsync(c->d_vbest, 0xFF, np, c->stream));
-    if (!in->wmask) CUDA_TRY(c, cudaMemsetAsync(c->d_wmask, 0, np * sizeof(uint32_t), c->stream));
-    if (!in->choice) CUDA_TRY(c, cudaMemsetAsync(c->d_choice, 8, np, c->stream));
+    if (!in->cost) CUDA_TRY(c, cudaMemsetAsync(c->d_cost, 0, ns * sizeof(float), c->stream));
+    if (!in->sel) CUDA_TRY(c, cudaMemsetAsync(c->d_sel, 0, ns * sizeof(uint32_t), c->stream));
+    if (!in->vbest) CUDA_TRY(c, cudaMemsetAsync(c->d_vbest, 0xFF, ns, c->stream));
+    if (!in->wmask) CUDA_TRY(c, cudaMemsetAsync(c->d_wmask, 0, ns * sizeof(uint32_t), c->stream));
+    if (!in->choice) CUDA_TRY(c, cudaMemsetAsync(c->d_choice, 8, ns, c->stream));
   }
   c->t = in->t;
   c->initialized = true;
@@ -489,7 +493,7 @@ AMH_API int amh_read_maps(amh_ctx* c, float* depth, float* normal3, float* cost,
   const size_t np = (size_t)c->W * c->H;
   if (depth || normal3) {
     if (mem == AMH_MEM_DEVICE) {
-      split_maps_kernel<<<1024, 256, 0, c->stream>>>(c->d_plane, np, depth, normal3);
+      split_maps_kernel<<<1024, 256, 0, c->stream>>>(c->d_plane, c->W, c->H, depth, normal3);
       int rc = launch_check(c, "split_maps");
       if (rc) return rc;
     } else {
@@ -497,7 +501,7 @@ AMH_API int amh_read_maps(amh_ctx* c, float* depth, float* normal3, float* cost,
       float* dn = nullptr;
       if (depth) CUDA_TRY(c, cudaMallocAsync(&dd, np * sizeof(float), c->stream));
       if (normal3) CUDA_TRY(c, cudaMallocAsync(&dn, np * 3 * sizeof(float), c->stream));
-      split_maps_kernel<<<1024, 256, 0, c->stream>>>(c->d_plane, np, dd, dn);
+      split_maps_kernel<<<1024, 256, 0, c->stream>>>(c->d_plane, c->W, c->H, dd, dn);
       int rc = launch_check(c, "split_maps");
       if (!rc && depth) CUDA_TRY(c, cudaMemcpyAsync(depth, dd, np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
       if (!rc && normal3)
@@ -507,9 +511,8 @@ AMH_API int amh_read_maps(amh_ctx* c, float* depth, float* normal3, float* cost,
       if (rc) return rc;
     }
   }
-  const cudaMemcpyKind k = mem == AMH_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (cost) CUDA_TRY(c, cudaMemcpyAsync(cost, c->d_cost, np * sizeof(float), k, c->stream));
-  if (selected) CUDA_TRY(c, cudaMemcpyAsync(selected, c->d_wmask, np * sizeof(uint32_t), k, c->stream));
+  if (cost) CUDA_TRY(c, export_state_field(c->d_cost, cost, c->W, c->H, 4, mem == AMH_MEM_HOST, c->stream));
+  if (selected) CUDA_TRY(c, export_state_field(c->d_wmask, selected, c->W, c->H, 4, mem == AMH_MEM_HOST, c->stream));
   if (mem == AMH_MEM_HOST) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return AMH_OK;
 }

@@ -24,6 +24,7 @@
 
 #include "amh.h"
 #include "amh_device.cuh"
+#include "amh_kernels.h"
 #include "amh_update.cuh"
 
 namespace amh {
@@ -191,7 +192,7 @@ struct amh_batch {
   uint8_t* d_vbest = nullptr;
   uint32_t* d_wmask = nullptr;
   uint8_t* d_choice = nullptr;
-  std::vector<size_t> px0;                // first pixel of each reference in the state arrays
+  std::vector<size_t> px0;                // first entry of each reference in the state arrays (state_index layout)
   ViewConst* d_views = nullptr;
   RefArgs* d_refs[AMH_BATCH_VARIANTS] = {};   // work lists, per variant (by its tile width)
   int items[AMH_BATCH_VARIANTS] = {};
@@ -439,7 +440,7 @@ AMH_API int amh_batch_create(amh_batch** out, const amh_params* p, int32_t n_vie
     b->H.push_back(cr.height);
     b->N.push_back(src_offsets[r + 1] - src_offsets[r]);
     b->px0[r] = b->total_px;
-    b->total_px += (size_t)cr.width * cr.height;
+    b->total_px += state_size(cr.width, cr.height);
   }
   const size_t NP = b->total_px;
   CB(cudaMalloc(&b->d_plane, NP * sizeof(float4)));
@@ -669,14 +670,15 @@ AMH_API int amh_batch_get_state(amh_batch* b, int32_t r, amh_state* o, int32_t m
   if (!b || !o) return AMH_EINVAL;
   if (r < 0 || r >= b->n_refs) return bfail(b, AMH_EINVAL, "reference index out of range");
   if (mem != AMH_MEM_HOST && mem != AMH_MEM_DEVICE) return bfail(b, AMH_EINVAL, "bad memory kind");
-  const size_t np = (size_t)b->W[r] * b->H[r], o0 = b->px0[r];
-  const cudaMemcpyKind k = mem == AMH_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (o->plane) BTRY(b, cudaMemcpyAsync(o->plane, b->d_plane + o0, np * sizeof(float4), k, b->stream));
-  if (o->cost) BTRY(b, cudaMemcpyAsync(o->cost, b->d_cost + o0, np * sizeof(float), k, b->stream));
-  if (o->sel) BTRY(b, cudaMemcpyAsync(o->sel, b->d_sel + o0, np * sizeof(uint32_t), k, b->stream));
-  if (o->vbest) BTRY(b, cudaMemcpyAsync(o->vbest, b->d_vbest + o0, np, k, b->stream));
-  if (o->wmask) BTRY(b, cudaMemcpyAsync(o->wmask, b->d_wmask + o0, np * sizeof(uint32_t), k, b->stream));
-  if (o->choice) BTRY(b, cudaMemcpyAsync(o->choice, b->d_choice + o0, np, k, b->stream));
+  const size_t o0 = b->px0[r];
+  const int W = b->W[r], H = b->H[r];
+  const bool host = mem == AMH_MEM_HOST;
+  if (o->plane) BTRY(b, export_state_field(b->d_plane + o0, o->plane, W, H, 16, host, b->stream));
+  if (o->cost) BTRY(b, export_state_field(b->d_cost + o0, o->cost, W, H, 4, host, b->stream));
+  if (o->sel) BTRY(b, export_state_field(b->d_sel + o0, o->sel, W, H, 4, host, b->stream));
+  if (o->vbest) BTRY(b, export_state_field(b->d_vbest + o0, o->vbest, W, H, 1, host, b->stream));
+  if (o->wmask) BTRY(b, export_state_field(b->d_wmask + o0, o->wmask, W, H, 4, host, b->stream));
+  if (o->choice) BTRY(b, export_state_field(b->d_choice + o0, o->choice, W, H, 1, host, b->stream));
   o->t = b->t;
   if (mem == AMH_MEM_HOST) BTRY(b, cudaStreamSynchronize(b->stream));
   return AMH_OK;

@@ -21,6 +21,26 @@ constexpr float kWorst = 2.0f;           // cost of an invalid (hypothesis, view
 constexpr int kMaxRefine = 6;
 constexpr int kPairCounters = 64;        // striped evaluation counters
 
+// Layout of the per-pixel state (plane, cost, S, v, selected views, winning
+// row): each row holds its pixels of colour 0 ((x + y) even), then its
+// pixels of colour 1, each run W2 = ceil(W / 2) entries long.  A checkerboard
+// phase then reads and writes whole sectors of its own colour and leaves the
+// other colour's sectors clean, where a row-major layout would dirty every
+// sector with half of its bytes.  The library's calls take and return
+// row-major maps; only the kernels see this layout.
+__host__ __device__ __forceinline__ size_t state_size(int W, int H) { return (size_t)H * 2 * (size_t)((W + 1) >> 1); }
+__host__ __device__ __forceinline__ size_t state_index(int x, int y, int W) {
+  const size_t w2 = (size_t)((W + 1) >> 1);
+  return (size_t)y * 2 * w2 + (((x + y) & 1) ? w2 : 0) + (size_t)(x >> 1);
+}
+// the pixel of a state index (the inverse of state_index on the image)
+__host__ __device__ __forceinline__ void state_pixel(size_t i, int W, int* x, int* y) {
+  const size_t w2 = (size_t)((W + 1) >> 1), r = i % (2 * w2);
+  *y = (int)(i / (2 * w2));
+  const int colour = r >= w2 ? 1 : 0;
+  *x = 2 * (int)(r - (colour ? w2 : 0)) + ((colour ^ *y) & 1);
+}
+
 // One source view.  A and b give the homography of a plane (n, d) as
 // H = A - b c^T with c = K_ref^-T n / d (Sec. 2: planes in scene space), where
 // A = K_j R_jr K_ref^-1 and b = K_j t_jr; P = K_j R_jr.  Rows 0 and 1 of A, b

@@ -137,4 +137,58 @@ int launch_phase(const PhaseArgs& a, cudaStream_t s) {
   }
 }
 
+namespace {
+// conversion between the state layout and row-major maps
+template <class T>
+__global__ void state_to_rows_kernel(const T* __restrict__ st, T* __restrict__ rows, int W, int H) {
+  const size_t n = (size_t)W * H;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    rows[i] = st[state_index((int)(i % W), (int)(i / W), W)];
+}
+template <class T>
+__global__ void rows_to_state_kernel(const T* __restrict__ rows, T* __restrict__ st, int W, int H) {
+  const size_t n = (size_t)W * H;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    st[state_index((int)(i % W), (int)(i / W), W)] = rows[i];
+}
+template <class T>
+void launch_convert(const void* src, void* dst, int W, int H, bool to_rows, cudaStream_t s) {
+  if (to_rows)
+    state_to_rows_kernel<T><<<1024, 256, 0, s>>>(static_cast<const T*>(src), static_cast<T*>(dst), W, H);
+  else
+    rows_to_state_kernel<T><<<1024, 256, 0, s>>>(static_cast<const T*>(src), static_cast<T*>(dst), W, H);
+}
+cudaError_t convert(const void* src, void* dst, int W, int H, int elem, bool to_rows, cudaStream_t s) {
+  switch (elem) {
+    case 16: launch_convert<float4>(src, dst, W, H, to_rows, s); break;
+    case 4: launch_convert<uint32_t>(src, dst, W, H, to_rows, s); break;
+    case 1: launch_convert<uint8_t>(src, dst, W, H, to_rows, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t export_state_field(const void* state, void* rows, int W, int H, int elem, bool host, cudaStream_t s) {
+  if (!host) return convert(state, rows, W, H, elem, true, s);
+  const size_t bytes = (size_t)W * H * elem;
+  void* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&tmp, bytes, s);
+  if (e != cudaSuccess) return e;
+  e = convert(state, tmp, W, H, elem, true, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rows, tmp, bytes, cudaMemcpyDeviceToHost, s);
+  const cudaError_t f = cudaFreeAsync(tmp, s);
+  return e != cudaSuccess ? e : f;
+}
+cudaError_t import_state_field(const void* rows, void* state, int W, int H, int elem, bool host, cudaStream_t s) {
+  if (!host) return convert(rows, state, W, H, elem, false, s);
+  const size_t bytes = (size_t)W * H * elem;
+  void* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&tmp, bytes, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(tmp, rows, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = convert(tmp, state, W, H, elem, false, s);
+  const cudaError_t f = cudaFreeAsync(tmp, s);
+  return e != cudaSuccess ? e : f;
+}
 }  // namespace amh

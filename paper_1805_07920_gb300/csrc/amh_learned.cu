@@ -159,19 +159,20 @@ __global__ void adam_kernel(float* w, float* m, float* v, const float* g, __nv_b
 
 // Features of half-resolution pixel (X, Y), read at full-resolution pixel
 // (2X, 2Y): intensity / 255 - 0.5, normalised log depth, normal, cost / 2,
-// zeros up to 16 channels.  Also keeps the input plane for the head.
+// zeros up to 16 channels.  Also keeps the input plane for the head.  The
+// plane and cost come from the context's state (state_index layout).
 __global__ void features_kernel(const void* ref, int ref_half, const float4* plane, const float* cost, int W, int H,
                                 int w2, int h2, float lmid, float lscale, __nv_bfloat16* x0, float4* pin) {
   const int n = w2 * h2;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int X = p % w2, Y = p / w2;
     const int x = min(2 * X, W - 1), y = min(2 * Y, H - 1);
-    const size_t q = (size_t)y * W + x;
+    const size_t q = (size_t)y * W + x, qs = state_index(x, y, W);   // image, state
     const float I = ref_half ? __half2float(reinterpret_cast<const __half*>(ref)[q])
                              : (float)reinterpret_cast<const uint8_t*>(ref)[q];
-    const float4 pl = plane[q];
+    const float4 pl = plane[qs];
     const float f[6] = {I / 255.f - 0.5f, (logf(fmaxf(pl.w, 1e-6f)) - lmid) * lscale, pl.x, pl.y, pl.z,
-                        cost[q] * 0.5f};
+                        cost[qs] * 0.5f};
     for (int c = 0; c < 16; c++) x0[(size_t)p * 16 + c] = __float2bfloat16(c < 6 ? f[c] : 0.f);
     pin[p] = pl;
   }
@@ -184,7 +185,7 @@ __global__ void targets_kernel(const float4* plane, const float* cost, const flo
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int X = p % w2, Y = p / w2;
     const int x = min(2 * X, W - 1), y = min(2 * Y, H - 1);
-    const size_t q = (size_t)y * W + x;
+    const size_t q = state_index(x, y, W);
     const float4 pf = plane[q], pi = pin[p];
     const bool ok = cost[q] < cmax && pf.w > 0.f && pi.w > 0.f;
     target[(size_t)p * 4 + 0] = ok ? logf(pf.w) - logf(pi.w) : 0.f;

@@ -30,10 +30,13 @@ constexpr int kMaxDevices = 64;
 float* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-__global__ void split_maps_to_scratch(const float4* __restrict__ plane, int64_t first, int64_t n,
+// pixels first .. first + n - 1 in row-major order, read from the state
+// (amh::state_index layout)
+__global__ void split_maps_to_scratch(const float4* __restrict__ plane, int W, int64_t first, int64_t n,
                                       float* __restrict__ scratch) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 p = plane[first + i];
+    const int64_t px = first + i;
+    const float4 p = plane[amh::state_index((int)(px % W), (int)(px / W), W)];
     scratch[i] = p.w;
     scratch[kMaxPixels + 3 * i] = p.x;
     scratch[kMaxPixels + 3 * i + 1] = p.y;
@@ -92,7 +95,7 @@ extern "C" AMH_API int amh_read_maps_noalloc(amh_ctx* c, float* depth, float* no
 
   int rc = AMH_OK;
   const int blocks = (int)((n_pixels + 255) / 256 < 1024 ? (n_pixels + 255) / 256 : 1024);
-  split_maps_to_scratch<<<blocks, 256, 0, c->stream>>>(c->d_plane, first_pixel, n_pixels, scratch);
+  split_maps_to_scratch<<<blocks, 256, 0, c->stream>>>(c->d_plane, c->W, first_pixel, n_pixels, scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) rc = set_err(c, AMH_ECUDA, "amh_read_maps_noalloc: launch", e);
   if (!rc && depth) {

@@ -46,6 +46,11 @@ static_assert(acp_dx(6) == 3 && acp_dy(6) == -4, "near up ends at (3, -4)");
 static_assert(acp_dx(15) == -2 && acp_dy(15) == -1, "near left (-2, -1)");
 static_assert(acp_dx(28) == 0 && acp_dy(28) == -3 && acp_dy(38) == -23, "far up strip 3..23");
 static_assert(acp_dx(71) == 23 && acp_dy(71) == 0, "far right ends at (23, 0)");
+// every candidate lies on the other colour of the checkerboard (odd dx + dy)
+__host__ __device__ constexpr bool acp_other_colour(int c = 0) {
+  return c == 72 ? true : (((acp_dx(c) + acp_dy(c)) & 1) != 0 && acp_other_colour(c + 1));
+}
+static_assert(acp_other_colour(), "propagation candidates lie on the other colour");
 
 // Reference window of one pixel (Sec. 3.3): 36 samples at offsets
 // {-5,-3,-1,1,3,5}^2 clamped to the image; w = exp(-|I - I_c| / (2 sigma_I^2)
@@ -591,11 +596,26 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   constexpr bool kStaged = (kMode & kStage) != 0;
   static_assert(!(kStaged && kTex), "the staged sweep gathers; the texture-filter form does not stage");
   const int N = a.N;
-  const size_t pi = live ? checked_index(a, (size_t)y * a.W + x, (size_t)a.W * a.H, kBadPixel) : 0;
+  // the pixel's state index (32-bit: a state holds fewer than 2^31 entries)
+  const int pi = live ? (int)checked_index(a, (size_t)(y * (2 * ((a.W + 1) >> 1)) + (((x + y) & 1) ? (a.W + 1) >> 1 : 0) +
+                                                       (x >> 1)),
+                                           state_size(a.W, a.H), kBadPixel)
+                      : 0;
   const float fx = (float)x, fy = (float)y;
   const float3 ray = ref_ray(a.Kinv, fx, fy);
 
   // --- Sec. 3.1: asymmetric checkerboard propagation ---------------------------
+  // pick[g]: pixel offset of region g's candidate from (x, y), packed as
+  // (dx + 32) | (dy + 32) << 8 (-1: none).  Every candidate offset has odd
+  // dx + dy, so every candidate lies on the other colour: its state index is
+  // the pixel's base, y S + (the other colour's run) + x / 2, plus
+  // dy S + ((x mod 2) + dx) / 2 (S = entries per state row).
+  const int srow = 2 * ((a.W + 1) >> 1), xodd = x & 1;
+  const int qbase = y * srow + (((x + y) & 1) ? 0 : (srow >> 1)) + (x >> 1);
+  auto pick_index = [&](int off) {
+    return checked_index(a, state_index(x + (off & 255) - 32, y + (off >> 8) - 32, a.W), state_size(a.W, a.H),
+                         kBadNeighbour);
+  };
   int pick[kRegions];
 #pragma unroll
   for (int g = 0; g < kRegions; g++) pick[g] = -1;
@@ -605,18 +625,19 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     int best = -1;
     if (kMode & kSymmetric) {
       const int dist = g < 4 ? 1 : 5, dir = g & 3;
-      const int qx = x + (dir == 2 ? -dist : dir == 3 ? dist : 0), qy = y + (dir == 0 ? -dist : dir == 1 ? dist : 0);
-      if (qx >= 0 && qy >= 0 && qx < a.W && qy < a.H)
-        best = (int)checked_index(a, (size_t)qy * a.W + qx, (size_t)a.W * a.H, kBadNeighbour);
+      const int dx = dir == 2 ? -dist : dir == 3 ? dist : 0, dy = dir == 0 ? -dist : dir == 1 ? dist : 0;
+      const int qx = x + dx, qy = y + dy;
+      if (qx >= 0 && qy >= 0 && qx < a.W && qy < a.H) best = (dx + 32) | (dy + 32) << 8;
     } else {
       float bc = 0.f;
 #pragma unroll
       for (int c = acp_start(g); c < acp_start(g + 1); c++) {
         const int qx = x + acp_dx(c), qy = y + acp_dy(c);
         if (qx < 0 || qy < 0 || qx >= a.W || qy >= a.H) continue;
-        const int q = (int)checked_index(a, (size_t)qy * a.W + qx, (size_t)a.W * a.H, kBadNeighbour);
+        const int q = (int)checked_index(a, (size_t)(qbase + acp_dy(c) * srow + ((xodd + acp_dx(c)) >> 1)),
+                                         state_size(a.W, a.H), kBadNeighbour);
         const float cq = __ldg(&a.cost[q]);
-        if (best < 0 || cq < bc) { best = q; bc = cq; }
+        if (best < 0 || cq < bc) { best = (acp_dx(c) + 32) | (acp_dy(c) + 32) << 8; bc = cq; }
       }
     }
     pick[g] = best;
@@ -628,10 +649,10 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   for (int g = 0; g < kRegions; g++) {
     hD[g] = 0.f;
     if (pick[g] < 0) continue;
-    const int q = pick[g];
-    const float4 pq = a.plane[q];
+    const float4 pq = a.plane[pick_index(pick[g])];
     const float3 nq = make_float3(pq.x, pq.y, pq.z);
-    const float3 rq = ref_ray(a.Kinv, (float)(q % a.W), (float)(q / a.W));
+    const int qx = x + (pick[g] & 255) - 32, qy = y + (pick[g] >> 8) - 32;
+    const float3 rq = ref_ray(a.Kinv, (float)qx, (float)qy);
     const float d = -pq.w * dot3(nq, rq);          // plane offset, the same at q and x
     const float den = dot3(nq, ray);
     if (!(den < 0.f)) continue;
@@ -701,7 +722,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     if (choice < 8) {
 #pragma unroll
       for (int g = 0; g < kRegions; g++) if (g == choice) bestD = hD[g];
-      const float4 pq = a.plane[pick[choice]];
+      const float4 pq = a.plane[pick_index(pick[choice])];
       best = make_float4(pq.x, pq.y, pq.z, bestD);
     }
     const int nc = a.t < 3 ? 1 : kMaxRefine;
@@ -768,7 +789,7 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
   if (choice < 8) {
 #pragma unroll
     for (int g = 0; g < kRegions; g++) if (g == choice) bestD = hD[g];
-    const float4 pq = a.plane[pick[choice]];
+    const float4 pq = a.plane[pick_index(pick[choice])];
     best = make_float4(pq.x, pq.y, pq.z, bestD);
   }
 
@@ -816,12 +837,14 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     best = bc < nc ? refine_candidate(a, x, y, best, ray, bc) : prop;
     choice = bc < nc ? 9 + bc : 15;
   }
-  a.plane[pi] = best;
-  a.cost[pi] = bm;
-  a.sel[pi] = St;
-  a.vbest[pi] = v < 0 ? (uint8_t)255 : (uint8_t)v;
-  a.wmask[pi] = wm;
-  a.choice[pi] = (uint8_t)choice;
+  // the pixel's new state: streaming stores, nothing reads it again in this
+  // phase
+  __stcs(&a.plane[pi], best);
+  __stcs(&a.cost[pi], bm);
+  __stcs(&a.sel[pi], St);
+  __stcs(&a.vbest[pi], v < 0 ? (uint8_t)255 : (uint8_t)v);
+  __stcs(&a.wmask[pi], wm);
+  __stcs(&a.choice[pi], (uint8_t)choice);
 }
 
 // Random initialisation of one pixel (Sec. 2, Gipuma-style random planes):
@@ -831,10 +854,10 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
 template <bool kHalf, bool kTex, class A>
 __device__ __forceinline__ void init_pixel(const A& a, PixelArrays& sm, int x, int y, int* npairs) {
   const int N = a.N;
-  const size_t pi = checked_index(a, (size_t)y * a.W + x, (size_t)a.W * a.H, kBadPixel);
+  const size_t pi = checked_index(a, state_index(x, y, a.W), state_size(a.W, a.H), kBadPixel);
   const float fx = (float)x, fy = (float)y;
   const float3 ray = ref_ray(a.Kinv, fx, fy);
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)pi, 0u, 0u, 0u), a.key0, a.key1);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)(y * a.W + x), 0u, 0u, 0u), a.key0, a.key1);
   const float3 n = face_camera(normal_from_uniforms(u01(r.y), u01(r.z)), ray);
   const float4 pl = make_float4(n.x, n.y, n.z, a.dmin + (a.dmax - a.dmin) * u01(r.x));
   float4 c;
