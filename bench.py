@@ -56,6 +56,7 @@ FP32_LANES_PER_SM = 128
 # and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
     "52a607e93d353ae7/fp32_blend": 213867776.0 + 147174656.0,         # profiles/phase_kernel_large.md
+    "52a607e93d353ae7/texture_bilinear": 213054208.0 + 143037696.0,   # profiles/phase_kernel_texture_large.md
 }
 
 
