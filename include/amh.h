@@ -295,6 +295,19 @@ AMH_API int amh_net_params(amh_net* net, int32_t layer, float* w, float* b, int3
 AMH_API int amh_net_grads(amh_net* net, int32_t layer, float* gw, float* gb);
 /* Features from host memory (stored as BF16). */
 AMH_API int amh_net_set_input(amh_net* net, const float* x0);
+/* One training example in a single call, from host or device memory (mem:
+ * AMH_MEM_HOST / AMH_MEM_DEVICE): features x (h2, w2, channels) FP32,
+ * channels 1..16 (the rest are zero; stored as BF16), targets (h2, w2, 4)
+ * FP32 and mask (h2, w2) u8, the layouts amh_net_features /
+ * amh_net_targets produce.  mirror bit 0 mirrors the example along x
+ * (columns reversed, the normal's x negated: feature 2 and target 1), bit 1
+ * along y (rows reversed, feature 3 and target 2): the augmentation of
+ * training.  The mirroring, padding and conversion run on the device; host
+ * inputs are copied first.  The call does not synchronise; the inputs must
+ * stay valid until the network's stream reaches it.  Errors: AMH_EINVAL for
+ * NULL pointers, channels outside 1..16 or a bad memory kind. */
+AMH_API int amh_net_set_example(amh_net* net, const float* x, int32_t channels, const float* target,
+                                const uint8_t* mask, int32_t mirror, int32_t mem);
 /* Features from the context's current state; also keeps that state's planes
  * as the base the outputs are residuals of. */
 AMH_API int amh_net_features(amh_net* net, amh_ctx* ctx);
@@ -338,8 +351,9 @@ AMH_API int amh_set_proposal(amh_ctx* ctx, const float* plane4, int32_t width2, 
  * in_d2 r2 d2 in_d1 r1 d1 out (in_* = pooled / upsampled inputs, r* = a
  * decoder layer's ReLU output before its skip; BF16 ones widened to FP32),
  * 32 + L the gradient at layer L's output after its ReLU mask (FP32, from the
- * last amh_net_backward).  Layout (H, W, C) of that level.  With out = NULL
- * the element count is written to *count; otherwise *count must equal it. */
+ * last amh_net_backward).  Layout (H, W, C) of that level.  which = 64: the
+ * targets (h2, w2, 4); 65: the mask (h2, w2) as 0 / 1.  With out = NULL the
+ * element count is written to *count; otherwise *count must equal it. */
 AMH_API int amh_net_read(amh_net* net, int32_t which, float* out, int64_t* count);
 /* Wait for the network's work. */
 AMH_API int amh_net_synchronize(amh_net* net);

@@ -34,7 +34,7 @@ EXPORTS = ["amh_default_params", "amh_create", "amh_set_stream", "amh_init_rando
            "amh_batch_iterate", "amh_batch_run", "amh_batch_set_variant", "amh_batch_autotune",
            "amh_batch_info", "amh_batch_get_state", "amh_batch_pair_count", "amh_batch_synchronize",
            "amh_batch_last_error", "amh_batch_destroy", "amh_net_create", "amh_net_params", "amh_net_grads",
-           "amh_net_set_input", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
+           "amh_net_set_input", "amh_net_set_example", "amh_net_features", "amh_net_targets", "amh_net_set_targets", "amh_net_forward",
            "amh_net_backward", "amh_net_adam", "amh_net_read", "amh_net_propose", "amh_clear_proposal", "amh_net_synchronize",
            "amh_net_last_error", "amh_net_destroy", "amh_gather_peak", "amh_median4", "amh_fuse", "amh_select_sources", "amh_set_proposal", "amh_bounds_checked"]
 
@@ -503,6 +503,7 @@ def _net_lib():
         L.amh_net_params.argtypes = [_vp, _i32, _vp, _vp, _i32]
         L.amh_net_grads.argtypes = [_vp, _i32, _vp, _vp]
         L.amh_net_set_input.argtypes = [_vp, _vp]
+        L.amh_net_set_example.argtypes = [_vp, _vp, _i32, _vp, _vp, _i32, _i32]
         L.amh_net_features.argtypes = [_vp, _vp]
         L.amh_net_targets.argtypes = [_vp, _vp, ctypes.c_float]
         L.amh_net_set_targets.argtypes = [_vp, _vp, _vp]
@@ -584,6 +585,36 @@ class Net:
         x = np.ascontiguousarray(x0, np.float32).reshape(self.h2, self.w2, 16)
         self._check(_net_lib().amh_net_set_input(self.ctx, _ptr(x)))
 
+    def set_example(self, x, target, mask, mirror_x=False, mirror_y=False):
+        """One training example (amh_net_set_example): features x (h2, w2, C)
+        float32 with C <= 16, targets (h2, w2, 4) float32, mask (h2, w2) uint8,
+        all numpy arrays or all CUDA tensors (which then must stay alive until
+        the network's stream has run the call); mirrored on the device."""
+        dev = _is_torch(x)
+        if dev:
+            import torch
+            ok = (x.dtype == torch.float32 and target.dtype == torch.float32 and mask.dtype == torch.uint8 and
+                  all(a.is_cuda and a.is_contiguous() for a in (x, target, mask)))
+            C = x.shape[-1]
+        else:
+            x = np.ascontiguousarray(x, np.float32)
+            target = np.ascontiguousarray(target, np.float32)
+            mask = np.ascontiguousarray(mask, np.uint8)
+            ok = True
+            C = x.shape[-1]
+        if not ok:
+            raise ValueError("set_example: float32 / float32 / uint8 contiguous CUDA tensors expected")
+        n = self.h2 * self.w2
+        if (x.numel() if dev else x.size) != n * C:
+            raise ValueError(f"set_example: features must be ({self.h2}, {self.w2}, C)")
+        if (target.numel() if dev else target.size) != n * 4 or (mask.numel() if dev else mask.size) != n:
+            raise ValueError(f"set_example: targets ({self.h2}, {self.w2}, 4) and mask ({self.h2}, {self.w2}) expected")
+        self._check(_net_lib().amh_net_set_example(self.ctx, _ptr(x), int(C), _ptr(target), _ptr(mask),
+                                                   (1 if mirror_x else 0) | (2 if mirror_y else 0),
+                                                   AMH_MEM_DEVICE if dev else AMH_MEM_HOST))
+        if not dev:
+            self.synchronize()
+
     def set_targets(self, target, mask):
         t = np.ascontiguousarray(target, np.float32).reshape(self.h2, self.w2, 4)
         m = np.ascontiguousarray(mask, np.uint8).reshape(self.h2, self.w2)
@@ -620,12 +651,14 @@ class Net:
 
     def read(self, name):
         """An internal tensor as float32 (H, W, C): a forward tensor of
-        NET_TENSORS, or "dy:<layer>" for the gradient at that layer's output
-        after its ReLU mask (from the last backward)."""
+        NET_TENSORS, "dy:<layer>" for the gradient at that layer's output
+        after its ReLU mask (from the last backward), or "target" / "mask"."""
         names = [n for n, _, _ in NET_LAYERS]
         if name.startswith("dy:"):
             L = names.index(name[3:])
             which, level, ch = 32 + L, self.LAYER_LEVEL[name[3:]], NET_LAYERS[L][2]
+        elif name in ("target", "mask"):
+            which, level, ch = (64, 0, 4) if name == "target" else (65, 0, 1)
         else:
             which = list(self.NET_TENSORS).index(name)
             level, ch = self.NET_TENSORS[name]

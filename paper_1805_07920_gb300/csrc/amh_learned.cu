@@ -177,6 +177,31 @@ __global__ void features_kernel(const void* ref, int ref_half, const float4* pla
     pin[p] = pl;
   }
 }
+// one training example, mirrored: output pixel (X, Y) reads source pixel
+// (w2 - 1 - X or X, h2 - 1 - Y or Y); an x mirror negates the normal's x
+// (feature 2, target 1), a y mirror its y (feature 3, target 2); features
+// padded to 16 channels and stored as BF16
+__global__ void example_kernel(const float* __restrict__ x, int C, const float* __restrict__ t,
+                               const uint8_t* __restrict__ m, int w2, int h2, int mirror, __nv_bfloat16* x0,
+                               float* target, uint8_t* mask) {
+  const int n = w2 * h2;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int X = p % w2, Y = p / w2;
+    const int sx = (mirror & 1) ? w2 - 1 - X : X, sy = (mirror & 2) ? h2 - 1 - Y : Y;
+    const size_t q = (size_t)sy * w2 + sx;
+    for (int c = 0; c < 16; c++) {
+      float v = c < C ? x[q * C + c] : 0.f;
+      if ((c == 2 && (mirror & 1)) || (c == 3 && (mirror & 2))) v = -v;
+      x0[(size_t)p * 16 + c] = __float2bfloat16(v);
+    }
+    for (int c = 0; c < 4; c++) {
+      float v = t[q * 4 + c];
+      if ((c == 1 && (mirror & 1)) || (c == 2 && (mirror & 2))) v = -v;
+      target[(size_t)p * 4 + c] = v;
+    }
+    mask[p] = m[q];
+  }
+}
 // targets: (log D_final - log D_in, n_final - n_in) where the final cost is
 // below cmax (confident pixels)
 __global__ void targets_kernel(const float4* plane, const float* cost, const float4* pin, int W, int H, int w2,
@@ -536,6 +561,29 @@ AMH_API int amh_net_set_input(amh_net* n, const float* x0_host) {
   return AMH_OK;
 }
 
+AMH_API int amh_net_set_example(amh_net* n, const float* x, int32_t channels, const float* target,
+                                const uint8_t* mask, int32_t mirror, int32_t mem) {
+  if (!n || !x || !target || !mask) return AMH_EINVAL;
+  if (channels < 1 || channels > 16) return nfail(n, AMH_EINVAL, "channels must be 1..16");
+  if (mem != AMH_MEM_HOST && mem != AMH_MEM_DEVICE) return nfail(n, AMH_EINVAL, "bad memory kind");
+  const size_t np = (size_t)n->w2 * n->h2;
+  const float *dx = x, *dt = target;
+  const uint8_t* dm = mask;
+  if (mem == AMH_MEM_HOST) {   // into the scratch buffers (gA: features, gB: targets, then the mask)
+    NTRY(n, cudaMemcpyAsync(n->gA, x, np * channels * 4, cudaMemcpyHostToDevice, n->stream));
+    NTRY(n, cudaMemcpyAsync(n->gB, target, np * 16, cudaMemcpyHostToDevice, n->stream));
+    uint8_t* mb = reinterpret_cast<uint8_t*>(n->gB + np * 4);
+    NTRY(n, cudaMemcpyAsync(mb, mask, np, cudaMemcpyHostToDevice, n->stream));
+    dx = n->gA;
+    dt = n->gB;
+    dm = mb;
+  }
+  example_kernel<<<blocks_for(np), 256, 0, n->stream>>>(dx, channels, dt, dm, n->w2, n->h2, mirror & 3, n->x0,
+                                                        n->target, n->mask);
+  NTRY(n, cudaGetLastError());
+  return AMH_OK;
+}
+
 AMH_API int amh_net_features(amh_net* n, amh_ctx* c) {
   if (!n || !c) return AMH_EINVAL;
   if ((c->W + 1) / 2 > n->w2 || (c->H + 1) / 2 > n->h2) return nfail(n, AMH_EINVAL, "context larger than the network");
@@ -704,8 +752,21 @@ AMH_API int amh_net_read(amh_net* n, int32_t which, float* out, int64_t* count) 
   constexpr int kAct = (int)(sizeof(act) / sizeof(act[0]));
   const size_t lp[kLayers] = {P0, P1, P2, P3, P2, P1, P0, P0};
   B src{};
+  if (which == 65) {   // the mask, as 0 / 1
+    if (!out) {
+      *count = (int64_t)P0;
+      return AMH_OK;
+    }
+    if (*count != (int64_t)P0) return nfail(n, AMH_EINVAL, "the mask has %zu elements", P0);
+    std::vector<uint8_t> h(P0);
+    NTRY(n, cudaMemcpyAsync(h.data(), n->mask, P0, cudaMemcpyDeviceToHost, n->stream));
+    NTRY(n, cudaStreamSynchronize(n->stream));
+    for (size_t i = 0; i < P0; i++) out[i] = (float)h[i];
+    return AMH_OK;
+  }
   if (which >= 0 && which < kAct) src = act[which];
   else if (which >= 32 && which < 32 + kLayers) src = B{nullptr, n->dy[which - 32], lp[which - 32] * kNet[which - 32].cout};
+  else if (which == 64) src = B{nullptr, n->target, P0 * 4};
   else return nfail(n, AMH_EINVAL, "unknown tensor %d", which);
   if (!out) {
     *count = (int64_t)src.n;

@@ -74,25 +74,15 @@ def targets(state_in_planes, state_final, w2, h2, cost_max=COST_MAX):
     return t, ok
 
 
-def _pad16(f):
-    out = np.zeros(f.shape[:2] + (16,), np.float32)
-    out[..., :f.shape[2]] = f
+def _to_device(examples):
+    """Examples as CUDA tensors (features float32, targets float32, mask
+    uint8), uploaded once; amh_net_set_example mirrors them on the device."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = [tuple(torch.from_numpy(np.ascontiguousarray(a, dt)).to(dev) for a, dt in
+                 ((f, np.float32), (t, np.float32), (m, np.uint8))) for f, t, m in examples]
+    torch.cuda.synchronize()
     return out
-
-
-def _flip(f, t, m, fx, fy):
-    """Mirror an example: x mirror negates the normal's x (feature 2, target
-    1), y mirror its y (feature 3, target 2)."""
-    f, t = f.copy(), t.copy()
-    if fx:
-        f, t, m = f[:, ::-1], t[:, ::-1], m[:, ::-1]
-        f[..., 2] *= -1
-        t[..., 1] *= -1
-    if fy:
-        f, t, m = f[::-1], t[::-1], m[::-1]
-        f[..., 3] *= -1
-        t[..., 2] *= -1
-    return np.ascontiguousarray(f), np.ascontiguousarray(t), np.ascontiguousarray(m)
 
 
 def plain_example(scene, seed):
@@ -137,25 +127,24 @@ def train(out_dir, n_scenes=200, width=1600, height=1056, steps=8000, lr=1e-3, s
     net = amh.Net(w2, h2, seed=seed)
     rng = np.random.default_rng(seed)
     hist, val_hist = [], []
+    train_dev, val_dev = _to_device(train_ex), _to_device(val_ex)
 
     def val_loss():
         tot = 0.0
-        for f, t, m in val_ex:
-            net.set_input(_pad16(f.astype(np.float32)))
-            net.set_targets(t, m)
+        for x, t, m in val_dev:
+            net.set_example(x, t, m)
             net.forward()
             tot += net.backward()
-        return tot / len(val_ex)
+        return tot / len(val_dev)
 
     v0 = val_loss()
     val_hist.append((0, v0))
     log(f"val loss at start {v0:.4f} (zero-residual loss {np.mean([np.abs(t).sum(-1)[m > 0].mean() for _, t, m in val_ex]):.4f})")
     t0 = time.time()
     for it in range(1, steps + 1):
-        f, t, m = train_ex[int(rng.integers(len(train_ex)))]
-        f, t, m = _flip(f.astype(np.float32), t, m, rng.random() < 0.5, rng.random() < 0.5)
-        net.set_input(_pad16(f))
-        net.set_targets(t, m)
+        x, t, m = train_dev[int(rng.integers(len(train_dev)))]
+        mirror_x, mirror_y = rng.random() < 0.5, rng.random() < 0.5     # random x / y mirroring
+        net.set_example(x, t, m, mirror_x, mirror_y)
         net.forward()
         loss = net.backward()
         cur = lr * 0.5 * (1 + np.cos(np.pi * (it - 1) / steps))     # cosine decay

@@ -326,3 +326,43 @@ def test_net_rejects_bad_arguments(amh):
         amh.Net(60, 40)            # not a multiple of 8
     with pytest.raises(amh.AmhError):
         amh.Net(0, 8)
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_set_example_mirrors_on_the_device(amh, device):
+    """amh_net_set_example against the host-side reference of the training
+    augmentation: columns (rows) reversed for an x (y) mirror, the normal's x
+    (y) negated in feature 2 (3) and target 1 (2), features padded to 16
+    channels and stored as BF16 (round to nearest even); targets and mask
+    exactly."""
+    import torch
+    r = np.random.default_rng(11)
+    net = amh.Net(W2, H2, seed=3)
+    f = r.normal(0, 1, (H2, W2, 6)).astype(np.float32)
+    t = r.normal(0, 1, (H2, W2, 4)).astype(np.float32)
+    m = (r.random((H2, W2)) < 0.6).astype(np.uint8)
+    for mx in (False, True):
+        for my in (False, True):
+            ef, et, em = f.copy(), t.copy(), m.copy()
+            if mx:
+                ef, et, em = ef[:, ::-1].copy(), et[:, ::-1].copy(), em[:, ::-1].copy()
+                ef[..., 2] *= -1
+                et[..., 1] *= -1
+            if my:
+                ef, et, em = ef[::-1].copy(), et[::-1].copy(), em[::-1].copy()
+                ef[..., 3] *= -1
+                et[..., 2] *= -1
+            x0 = np.zeros((H2, W2, 16), np.float32)
+            x0[..., :6] = ef
+            x0 = torch.from_numpy(x0).to(torch.bfloat16).float().numpy()
+            if device:
+                dev = [torch.from_numpy(a).cuda() for a in (f, t, m)]
+                net.set_example(*dev, mirror_x=mx, mirror_y=my)
+                net.synchronize()
+            else:
+                net.set_example(f, t, m, mirror_x=mx, mirror_y=my)
+            assert np.array_equal(net.read("x0"), x0), (mx, my)
+            assert np.array_equal(net.read("target"), et), (mx, my)
+            assert np.array_equal(net.read("mask")[..., 0], em.astype(np.float32)), (mx, my)
+    net.close()
+
