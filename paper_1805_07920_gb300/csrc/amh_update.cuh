@@ -808,28 +808,44 @@ __device__ __forceinline__ void update_pixel(const A& a, PixelArrays& sm, int x,
     prop = make_float4(pr.x, pr.y, pr.z, Dx);
   }
   const int ncand = nc + (has_prop ? 1 : 0);
-  int bc = -1;
-  float bcm = 0.f;
-  // A candidate can only change the outcome if its cost ends strictly below
-  // both the current best and the best candidate so far.  Its weighted sum
-  // only grows view by view (w_j >= 0, m_j >= 0, and rounding is monotone),
-  // so once sum * inv_sw reaches that bound it has lost: its remaining views
-  // are skipped, and the result is exactly that of the full evaluation.
+  // The outcome is the candidate of least cost strictly below the current
+  // best (ties: the lower index).  The candidates are scored view by view:
+  // for each view (warp-uniform: one texture per gather) a lane runs only its
+  // own live candidates, so the warp pays for its busiest lane rather than
+  // for every candidate some lane still needs.  A candidate's weighted sum
+  // runs over the views in the same order as alone and only grows (w_j >= 0,
+  // m_j >= 0, rounding is monotone), so one that reaches the current best
+  // has lost and is dropped: every sum that is kept, and so the outcome, is
+  // exactly that of scoring each candidate in full.  The candidates' planes
+  // take the propagated rows' slots and their sums the first matrix row,
+  // both no longer read.
+  uint32_t okm = 0u;
 #pragma unroll 1
   for (int ci = 0; ci < ncand; ci++) {
-    ok = plane_c(a.Kinv, ci < nc ? refine_candidate(a, x, y, best, ray, ci) : prop, ray, &c);
-    const float bound = bc < 0 ? bm : fminf(bm, bcm);
-    float m = 0.f;
-    bool alive = true;
-    for (int j = 0; j < N; j++) {   // j stays warp-uniform (one texture per gather)
-      const float wj = sm.wt(j);
-      if (wj > 0.f && alive) {
-        m = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], c, ok, ray, rw, npairs), m);
-        alive = m * inv_sw < bound;
-      }
+    float4 cc;
+    if (plane_c(a.Kinv, ci < nc ? refine_candidate(a, x, y, best, ray, ci) : prop, ray, &cc)) okm |= 1u << ci;
+    sm.cc(ci) = cc;
+    sm.m(0, ci, N) = 0.f;
+  }
+  uint32_t cand_live = (1u << ncand) - 1u;
+#pragma unroll 1
+  for (int j = 0; j < N; j++) {
+    const float wj = sm.wt(j);
+    uint32_t todo = wj > 0.f ? cand_live : 0u;
+    while (todo) {
+      const int ci = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const float m = fmaf(wj, ncc_cost<kHalf, kTex>(a.v[j], sm.cc(ci), (okm >> ci) & 1u, ray, rw, npairs),
+                           sm.m(0, ci, N));
+      sm.m(0, ci, N) = m;
+      if (!(m * inv_sw < bm)) cand_live &= ~(1u << ci);
     }
-    if (!alive) continue;
-    m *= inv_sw;
+  }
+  int bc = -1;
+  float bcm = 0.f;
+  for (int ci = 0; ci < ncand; ci++) {
+    if (!(cand_live >> ci & 1u)) continue;
+    const float m = sm.m(0, ci, N) * inv_sw;
     if (bc < 0 || m < bcm) { bc = ci; bcm = m; }
   }
   if (bc >= 0 && bcm < bm) {
