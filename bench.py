@@ -55,8 +55,8 @@ FP32_LANES_PER_SM = 128
 # capture, keyed by the hash of the phase kernel's sources it was taken on
 # and the interpolation form (null whenever the sources changed since).
 KNOWN_TRAFFIC: dict[str, float] = {
-    "52a607e93d353ae7/fp32_blend": 213867776.0 + 147174656.0,         # profiles/phase_kernel_large.md
-    "52a607e93d353ae7/texture_bilinear": 213054208.0 + 143037696.0,   # profiles/phase_kernel_texture_large.md
+    "443431915a570157/fp32_blend": 212933120.0 + 145355264.0,         # profiles/phase_kernel_large.md
+    "443431915a570157/texture_bilinear": 213670656.0 + 146705664.0,   # profiles/phase_kernel_texture_large.md
 }
 
 
