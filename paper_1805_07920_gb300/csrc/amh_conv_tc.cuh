@@ -7,16 +7,16 @@
 // channels ci of X (pixel + off(t), ci) W (t, co, ci), one MMA per tap and 16
 // input channels (M = 128 pixels of one row, N = a block of output channels,
 // K = 16).  Both operands sit in shared memory in the tensor cores' K-major
-// layout without swizzling: 8 x 16-byte core matrices, rows 16 bytes apart
-// along M / N, planes of 8 channels along K.  The forward / data-gradient
+// layout, in blocks of 64 channels (128-byte rows, 128-byte swizzle; a 16- or
+// 32-channel remainder in 32- or 64-byte rows).  The forward / data-gradient
 // kernel keeps its block of weights resident and streams input rows with a
 // one-pixel halo, each row loaded once per run of vertically adjacent tiles
 // (its comment below gives the schedule); the weight-gradient kernel streams
-// pixel chunks of channel-major copies.  A producer warp issues the TMA
-// copies, an MMA warp consumes them and recycles each buffer once the MMAs
-// that read it have committed, and the epilogue warps read the accumulator
-// with tcgen05.ld and apply bias, ReLU, skip addition and the BF16 / FP32
-// stores.
+// 64-pixel chunks of the same pixel-major tensors as MN-major operands.  A
+// producer warp issues the TMA copies, an MMA warp consumes them and recycles
+// each buffer once the MMAs that read it have committed, and the epilogue
+// warps read the accumulator with tcgen05.ld and apply bias, ReLU, skip
+// addition and the BF16 / FP32 stores.
 //
 // Layout: activations (H, W, C) BF16 with C a multiple of 16; weights (9,
 // Cout, Cin) BF16, tap t = 3 (dy + 1) + (dx + 1); Cout a multiple of 16, at
@@ -32,17 +32,8 @@ namespace amh {
 namespace tc {
 
 constexpr int kM = 128;          // pixels per CTA (rows of the accumulator)
-constexpr int kStages = 6;       // shared-memory ring
 constexpr int kMaxCout = 128;
 constexpr uint32_t kWaitTries = 1u << 24;
-
-// one ring stage: the activation and weight boxes of one K step, each as two
-// halves of 8 channels x 16 bytes per row
-struct alignas(1024) Stage {
-  uint8_t a[2][kM * 16];
-  uint8_t b[2][kMaxCout * 16];
-};
-constexpr size_t kSmemBytes = kStages * sizeof(Stage) + 1024;   // + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -114,6 +105,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+// 16 consecutive accumulator columns of this thread's TMEM lane (the warp
+// reads its lane quarter); the caller waits with tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -358,12 +359,7 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
         if (!(ok = mbar_wait(&acc_full[b], (tc >> 1) & 1u, 64))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t v[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tmem + b * ncols + ((uint32_t)(qw * 32) << 16) + (uint32_t)c0));
+        tmem_ld16(tmem + b * ncols + ((uint32_t)(qw * 32) << 16) + (uint32_t)c0, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         // buffer b may be overwritten by the next tile's MMAs once every
         // epilogue warp has its values
@@ -415,40 +411,78 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
 }
 
 // Weight gradient of a 3x3 convolution on the tensor cores:
-// dW (t, co, ci) = sum over pixels p of dy (p, co) x (p + off(t), ci), one
-// tap per blockIdx.y and a band of rows per blockIdx.x, as a GEMM with M =
-// Cout (the accumulator's rows; rows past Cout are left over and ignored), N
-// = Cin and K = the band's pixels, 16 per step.  The operands come
-// transposed, channel-major: dyT (Cout, H, Wp) and three copies of x,
-// xT_s (Cin, H, Wp) with xT_s (c, y, x) = x (y, x + s, c) for s = -1, 0, 1
-// (zero where x + s leaves the row), BF16, rows padded to Wp (a multiple of
-// 8).  A K step is two TMA boxes of 8 pixels x the channels per operand, in
-// the same K-major layout as the forward kernel.  The tap's column offset is
-// taken by the copy xT_dx, so every box starts at a pixel index that is a
-// multiple of 8 (a TMA box must start on a 16-byte boundary in its innermost
-// dimension); its row offset shifts the box's row coordinate, and rows
-// outside the image read zeros, as do pixels past the row's end.  The band's
-// sum is added into dw (FP32) by the epilogue warps.
+// dW (t, co, ci) = sum over pixels p of dy (p, co) x (p + off(t), ci), as
+// GEMMs with K = pixels, read straight from the pixel-major BF16 tensors
+// dy (H, W, Cout) and x (H, W, Cin): both operands are MN-major (the channel
+// is the contiguous dimension, a pixel is a row of the shared-memory tile).
+// Substituting y' = y + dy, dW (dy, dx) = sum over (y', x) of
+// dy (y' - dy, x, co) x (y', x + dx, ci): a K step is 64 pixels x .. x + 63
+// of one row y'.  B is one box of x at row y', pixels x - 1 .. x + 64, read
+// by three MMAs whose start rows differ by one pixel (dx = -1, 0, 1: one
+// accumulator each; the swizzle follows the shared-memory address bits, so
+// a start moved by whole rows reads what the TMA wrote); A the box(es) of
+// dy at rows y' - dy.  Rows and pixels outside the image read zeros.
+// With Cout <= 32 the three vertical taps share one MMA: A's rows 32 g + co
+// hold dy at row y' - (g - 1), so one CTA computes all nine taps from one
+// load of each operand per step (rows past Cout in each group are left over
+// and ignored); otherwise blockIdx.y is the vertical tap and A is one or two
+// boxes of 64 channels.  blockIdx.x is a band of rows y'.  Per step 4 x 3
+// MMAs of 16 pixels.  The band's sums are added into dw (FP32) by the
+// epilogue warps with vector atomics.  blockIdx.x takes an equal share of
+// the (row, 64-pixel chunk) steps, in row order.
+//
+// Channel boxes: Cout (stacked) or 64 channels of dy, min(Cin, 64) channels
+// of x, rows of 2 x channels bytes with the matching swizzle; a box of dy is
+// 64 pixel rows, one of x 66 (72 reserved, a whole number of swizzle
+// atoms); boxes along the channels lie one box apart (the MN stride of the
+// descriptor), groups of 8 pixels one 8-row group apart.
+constexpr int kWgMaxStages = 8;
+constexpr size_t kWgA = 128 * 128;                        // A: 128 channel rows x 64 pixels
+__host__ __device__ constexpr int wgrad_xbox(int cin) { return cin < 64 ? cin : 64; }
+constexpr int kWgXRows = 72;                              // x box: 66 pixels, 72 rows reserved
+__host__ __device__ constexpr size_t wgrad_xbox_bytes(int cin) { return (size_t)kWgXRows * 2 * wgrad_xbox(cin); }
+__host__ __device__ constexpr size_t wgrad_stage_bytes(int cin) {
+  return (kWgA + (size_t)((cin + 63) / 64) * wgrad_xbox_bytes(cin) + 1023) & ~size_t(1023);
+}
+__host__ __device__ constexpr uint32_t wgrad_acc_stride(int cin) { return cin <= 32 ? 32u : (uint32_t)cin; }
+__host__ __device__ constexpr uint32_t wgrad_tmem_cols(int cin) {
+  return 3 * wgrad_acc_stride(cin) <= 128 ? 128u : 3 * wgrad_acc_stride(cin) <= 256 ? 256u : 512u;
+}
+constexpr size_t kWgSmemCap = 200 * 1024;
+constexpr size_t kWgSlack = 1024;               // alignment of the ring
+__host__ __device__ constexpr int wgrad_stages(int cin) {
+  return (int)(kWgSmemCap / wgrad_stage_bytes(cin)) < kWgMaxStages ? (int)(kWgSmemCap / wgrad_stage_bytes(cin))
+                                                                      : kWgMaxStages;
+}
 struct WgradTcArgs {
   float* dw;                 // (9, Cout, Cin), accumulated into
   unsigned int* status;      // bit 0: a barrier wait gave up
-  int H, W, Cin, Cout, rows_per_band;
+  int H, W, Cin, Cout;
+  int steps_per_cta;         // (row, 64-pixel chunk) steps of one CTA
+  int stacked;               // Cout <= 32: the three vertical taps in one MMA
+  int S;                     // stages
 };
+// the low descriptor word of an MN-major operand: start address and the
+// stride between boxes along the channels
+__device__ __forceinline__ uint32_t desc_lo_mn(uint32_t addr, uint32_t box_bytes) {
+  return ((addr >> 4) & 0x3FFFu) | (((box_bytes >> 4) & 0x3FFFu) << 16);
+}
 
 __global__ void __launch_bounds__(kThreads) wgrad3x3_tc_kernel(const __grid_constant__ CUtensorMap tdy,
-                                                               const __grid_constant__ CUtensorMap tx_m1,
-                                                               const __grid_constant__ CUtensorMap tx_0,
-                                                               const __grid_constant__ CUtensorMap tx_p1,
+                                                               const __grid_constant__ CUtensorMap tx,
                                                                const WgradTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  Stage* st = reinterpret_cast<Stage*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full;
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[kWgMaxStages], empty[kWgMaxStages], acc_full;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int t = blockIdx.y, dy = t / 3 - 1, dx = t % 3 - 1;
-  const int y0 = blockIdx.x * a.rows_per_band, y1 = min(a.H, y0 + a.rows_per_band);
-  const int nseg = (a.W + 15) / 16, nk = (y1 > y0 ? y1 - y0 : 0) * nseg;
-  const uint32_t ncols = a.Cin <= 32 ? 32u : a.Cin <= 64 ? 64u : 128u;
+  const int S = a.S;
+  const uint32_t stage_bytes = (uint32_t)wgrad_stage_bytes(a.Cin), xb_bytes = (uint32_t)wgrad_xbox_bytes(a.Cin);
+  const int cba = a.stacked ? a.Cout : 64, cbb = wgrad_xbox(a.Cin);     // channels per box
+  const int dy_cta = a.stacked ? 0 : (int)blockIdx.y - 1;               // this CTA's vertical tap (not stacked)
+  const int nseg = (a.W + 63) / 64, k0 = blockIdx.x * a.steps_per_cta;
+  const int nk = max(0, min(a.H * nseg, k0 + a.steps_per_cta) - k0);
+  const uint32_t stride = wgrad_acc_stride(a.Cin), ncols = wgrad_tmem_cols(a.Cin);
 
   if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -456,7 +490,7 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_tc_kernel(const __grid_cons
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < kStages; s++) {
+    for (int s = 0; s < S; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -471,48 +505,66 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_tc_kernel(const __grid_cons
 
   if (warp == 4) {
     if (lane == 0) {
-      const uint32_t bytes = 2u * (uint32_t)(a.Cout + a.Cin) * 16u;
-      const CUtensorMap* tx = dx < 0 ? &tx_m1 : dx > 0 ? &tx_p1 : &tx_0;
-      for (int k = 0; k < nk && ok; k++) {
-        const int s = k % kStages;
-        if (!(ok = mbar_wait(&empty[s], ((uint32_t)(k / kStages) & 1u) ^ 1u))) break;
-        const int y = y0 + k / nseg, x0 = (k % nseg) * 16;
-        mbar_expect_tx(&full[s], bytes);
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          tma_load_3d(st[s].a[h], &tdy, x0 + 8 * h, y, 0, &full[s]);
-          tma_load_3d(st[s].b[h], tx, x0 + 8 * h, y + dy, 0, &full[s]);
+      const int na = a.stacked ? 3 : (a.Cout + 63) / 64, nbx = (a.Cin + 63) / 64;
+      const uint32_t bytes = (uint32_t)na * 128u * (uint32_t)cba + (uint32_t)nbx * 132u * (uint32_t)cbb;
+      RingPos q{0u, 0u};
+      for (int k = 0; k < nk && ok; k++, q = q.next((uint32_t)S)) {
+        if (!(ok = mbar_wait(&empty[q.slot], q.phase ^ 1u))) break;
+        const int y = (k0 + k) / nseg, x0 = ((k0 + k) % nseg) * 64;
+        uint8_t* st = ring + (size_t)q.slot * stage_bytes;
+        mbar_expect_tx(&full[q.slot], bytes);
+        if (a.stacked) {   // vertical tap g - 1 at A rows 32 g ..
+          for (int g = 0; g < 3; g++) tma_load_3d(st + (size_t)g * 4096, &tdy, 0, x0, y - (g - 1), &full[q.slot]);
+        } else {
+          for (int b = 0; b < na; b++) tma_load_3d(st + (size_t)b * 8192, &tdy, 64 * b, x0, y - dy_cta, &full[q.slot]);
         }
+        for (int b = 0; b < nbx; b++) tma_load_3d(st + kWgA + (size_t)b * xb_bytes, &tx, 64 * b, x0 - 1, y, &full[q.slot]);
       }
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      const uint32_t idesc = mma_idesc(kM, a.Cin);
-      for (int k = 0; k < nk && ok; k++) {
-        const int s = k % kStages;
-        if (!(ok = mbar_wait(&full[s], (uint32_t)(k / kStages) & 1u))) break;
+      const uint32_t idesc = mma_idesc(kM, a.Cin) | (1u << 15) | (1u << 16);   // A and B MN-major
+      const uint32_t a_hi = desc_hi(2u * (uint32_t)cba), b_hi = desc_hi(2u * (uint32_t)cbb);
+      const uint32_t a_lo = desc_lo_mn(smem_u32(ring), 128u * (uint32_t)cba);
+      const uint32_t b_lo = desc_lo_mn(smem_u32(ring) + (uint32_t)kWgA, xb_bytes);
+      // one pixel = one row of 2 x channels bytes, in 16-byte units
+      const uint32_t a_row = (uint32_t)cba >> 3, b_row = (uint32_t)cbb >> 3;
+      const uint32_t stage16 = stage_bytes >> 4;
+      RingPos q{0u, 0u};
+      for (int k = 0; k < nk && ok; k++, q = q.next((uint32_t)S)) {
+        if (!(ok = mbar_wait(&full[q.slot], q.phase))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        mma_bf16(tmem, smem_desc(smem_u32(st[s].a[0]), kM * 16, 128), smem_desc(smem_u32(st[s].b[0]), kMaxCout * 16, 128),
-                 idesc, k > 0 ? 1u : 0u);
-        mma_commit(&empty[s]);
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+          for (int dx = 0; dx < 3; dx++)
+            mma_bf16(tmem + (uint32_t)dx * stride, desc_pack(a_lo + q.slot * stage16 + 16u * a_row * c, a_hi),
+                     desc_pack(b_lo + q.slot * stage16 + (16u * c + (uint32_t)dx) * b_row, b_hi), idesc,
+                     (k > 0 || c > 0) ? 1u : 0u);
+        mma_commit(&empty[q.slot]);
       }
       if (ok) mma_commit(&acc_full);
     }
   } else if (nk > 0) {
-    if ((ok = mbar_wait(&acc_full, 0))) {
+    // epilogue: TMEM lane 32 w + l is A's row: (vertical tap w - 1, output
+    // channel l) when stacked, else output channel 32 w + l
+    const int g = a.stacked ? warp : dy_cta + 1, co = a.stacked ? lane : warp * 32 + lane;
+    const bool rows_used = a.stacked ? warp < 3 : warp * 32 < a.Cout;
+    if (rows_used && (ok = mbar_wait(&acc_full, 0, 64))) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int co = warp * 32 + lane;
-      for (int c0 = 0; c0 < a.Cin; c0 += 8) {
-        uint32_t v[8];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (co >= a.Cout) continue;
-        float* d = a.dw + ((size_t)t * a.Cout + co) * a.Cin + c0;
+      for (int dx = 0; dx < 3; dx++) {
+        float* d = a.dw + ((size_t)(3 * g + dx) * a.Cout + co) * a.Cin;
+        for (int c0 = 0; c0 < a.Cin; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)dx * stride + (uint32_t)c0, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (co >= a.Cout) continue;
 #pragma unroll
-        for (int e = 0; e < 8; e++) atomicAdd(d + e, __uint_as_float(v[e]));
+          for (int e = 0; e < 4; e++)
+            atomicAdd(reinterpret_cast<float4*>(d + c0) + e,
+                      make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]), __uint_as_float(v[4 * e + 2]),
+                                  __uint_as_float(v[4 * e + 3])));
+        }
       }
     }
   }
@@ -522,32 +574,6 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_tc_kernel(const __grid_cons
   if (warp == 5) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
-  }
-}
-
-// (P, C) -> (C, H, Wp) BF16 transpose of an activation or gradient map (P = H
-// W pixels; rows padded to Wp), shifted along the row by `shift`:
-// out (c, y, x) = in (y, x + shift, c), zero where x + shift leaves the row
-__global__ void __launch_bounds__(256) to_channel_major_kernel(const __nv_bfloat16* __restrict__ in,
-                                                               __nv_bfloat16* __restrict__ out, int H, int W, int Wp,
-                                                               int C, int shift) {
-  __shared__ __nv_bfloat16 tile[32][33];
-  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32, P = H * W;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int r = ty; r < 32; r += 8) {
-    const int p = p0 + r, c = c0 + tx;
-    tile[r][tx] = (p < P && c < C) ? in[(size_t)p * C + c] : __float2bfloat16(0.f);
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int c = c0 + r, p = p0 + tx;
-    if (c >= C || p >= P) continue;
-    // the output pixel whose shifted source is pixel p, and the row ends the
-    // shift uncovers
-    const int y = p / W, x = p % W - shift;
-    if (x >= 0 && x < W) out[((size_t)c * H + y) * Wp + x] = tile[tx][r];
-    if (shift > 0 && p % W == 0) out[((size_t)c * H + y) * Wp + W - 1] = __float2bfloat16(0.f);
-    if (shift < 0 && p % W == W - 1) out[((size_t)c * H + y) * Wp + 0] = __float2bfloat16(0.f);
   }
 }
 

@@ -9,8 +9,8 @@
 // (tcgen05.mma, FP32 accumulator in tensor memory, BF16 operands brought in by
 // the tensor memory accelerator; fused bias / ReLU / skip add), the data
 // gradient as the same convolution with flipped, transposed weights, the
-// weight gradient on the same tensor-core path from channel-major copies of
-// the operands (amh_conv_tc.cuh; bias gradients in FP32), 2x2 average pooling,
+// weight gradient on the same tensor-core path, reading the pixel-major
+// operands directly (amh_conv_tc.cuh; bias gradients in FP32), 2x2 average pooling,
 // nearest upsampling, the L1 loss, Adam, and the feature / head / proposal
 // conversions.
 //
@@ -281,10 +281,6 @@ struct amh_net {
   float *gA = nullptr, *gB = nullptr, *gE1 = nullptr, *gE2 = nullptr, *gE3 = nullptr;
   float* loss = nullptr;
   unsigned int* status = nullptr;         // bit 0: a convolution's barrier wait gave up
-  // channel-major operands of the weight gradient: x shifted by -1, 0, +1
-  // along the row, and dy
-  __nv_bfloat16* tX[3] = {};
-  __nv_bfloat16* tD = nullptr;
   size_t maxel = 0;
   std::vector<void*> allocs;
   std::string err;
@@ -405,38 +401,37 @@ int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
   return AMH_OK;
 }
-// (H, W, C) -> (C, H, Wp) channel-major copy shifted along the row by shift
-// (tc::to_channel_major_kernel)
-void to_cm(amh_net* n, const __nv_bfloat16* in, __nv_bfloat16* out, int H, int W, int Wp, int C, int shift) {
-  const int P = H * W;
-  tc::to_channel_major_kernel<<<dim3((P + 31) / 32, (C + 31) / 32), 256, 0, n->stream>>>(in, out, H, W, Wp, C, shift);
-}
 // weight gradient of layer L from its input x and its output gradient (FP32
-// dy for the bias, its BF16 copy dy16 for the weights): both operands are
-// turned channel-major, then the tensor-core kernel sums a band of rows per
-// CTA and tap into gw
+// dy for the bias, its BF16 copy dy16 for the weights): the tensor-core
+// kernel reads both pixel-major and sums a band of rows per CTA (all nine
+// taps when Cout <= 32, else the three of one vertical tap) into gw
 int wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, const __nv_bfloat16* dy16, int H, int W) {
-  const int Cin = kNet[L].cin, Cout = kNet[L].cout, np = H * W, Wp = (W + 7) & ~7;
-  CUtensorMap mdy, mx[3];
-  for (int s = 0; s < 3; s++) {
-    to_cm(n, x, n->tX[s], H, W, Wp, Cin, s - 1);
-    if (!bf16_map(&mx[s], n->tX[s], W, H, Cin, 8, 1, Cin, Wp)) return nfail(n, AMH_ECUDA, "wgrad: tensor map encoding failed");
-  }
-  to_cm(n, dy16, n->tD, H, W, Wp, Cout, 0);
-  if (!bf16_map(&mdy, n->tD, W, H, Cout, 8, 1, Cout, Wp)) return nfail(n, AMH_ECUDA, "wgrad: tensor map encoding failed");
+  const int Cin = kNet[L].cin, Cout = kNet[L].cout, np = H * W;
+  const int stacked = Cout <= 32 ? 1 : 0, cba = stacked ? Cout : 64, cbb = tc::wgrad_xbox(Cin);
+  CUtensorMap mdy, mx;
+  if (!bf16_map(&mdy, dy16, Cout, W, H, cba, 64, 1, 0, block_swizzle(cba)) ||
+      !bf16_map(&mx, x, Cin, W, H, cbb, 66, 1, 0, block_swizzle(cbb)))
+    return nfail(n, AMH_ECUDA, "wgrad: tensor map encoding failed");
+  const int S = tc::wgrad_stages(Cin);
+  const size_t smem = (size_t)S * tc::wgrad_stage_bytes(Cin) + tc::kWgSlack;
   int dev = 0;
   cudaGetDevice(&dev);
   static std::once_flag once[64];
-  std::call_once(once[dev & 63], [] {
-    cudaFuncSetAttribute(tc::wgrad3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes);
+  static cudaError_t attr_err[64] = {};
+  std::call_once(once[dev & 63], [dev] {
+    attr_err[dev & 63] = cudaFuncSetAttribute(tc::wgrad3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(tc::kWgSmemCap + tc::kWgSlack));
   });
+  if (attr_err[dev & 63] != cudaSuccess)
+    return nfail(n, AMH_ECUDA, "wgrad: shared-memory attribute: %s", cudaGetErrorString(attr_err[dev & 63]));
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  // about four CTAs per SM over the 9 taps, whole rows each
-  const int bands = std::max(1, std::min(H, 4 * n_sm / 9)), rows = (H + bands - 1) / bands;
-  const tc::WgradTcArgs a{n->gw[L], n->status, H, W, Cin, Cout, rows};
-  tc::wgrad3x3_tc_kernel<<<dim3((H + rows - 1) / rows, 9), tc::kThreads, tc::kSmemBytes, n->stream>>>(mdy, mx[0], mx[1],
-                                                                                                     mx[2], a);
+  // one CTA per SM (the ring takes most of the shared memory), each an equal
+  // share of the (row, 64-pixel chunk) steps
+  const int gy = stacked ? 1 : 3, steps = H * ((W + 63) / 64);
+  const int per_cta = (steps + std::max(1, n_sm / gy) - 1) / std::max(1, n_sm / gy);
+  const tc::WgradTcArgs a{n->gw[L], n->status, H, W, Cin, Cout, per_cta, stacked, S};
+  tc::wgrad3x3_tc_kernel<<<dim3((steps + per_cta - 1) / per_cta, gy), tc::kThreads, smem, n->stream>>>(mdy, mx, a);
   const int per_block = 2048, nb = (np + per_block - 1) / per_block;
   bias_grad_kernel<<<dim3((Cout + 31) / 32, nb), 256, 0, n->stream>>>(dy, np, Cout, per_block, n->gb[L]);
   const cudaError_t e = cudaGetLastError();
@@ -502,7 +497,6 @@ AMH_API int amh_net_create(amh_net** out, int32_t width2, int32_t height2, uint6
   NA(n->r1, P0 * 32); NA(n->d1, P0 * 32);
   n->maxel = P0 * 64;
   NA(n->g16, n->maxel); NA(n->gA, n->maxel); NA(n->gB, n->maxel);
-  NA(n->tX[0], n->maxel); NA(n->tX[1], n->maxel); NA(n->tX[2], n->maxel); NA(n->tD, n->maxel);
   {
     const size_t lp[kLayers] = {P0, P1, P2, P3, P2, P1, P0, P0};   // output size of each layer
     for (int L = 0; L < kLayers; L++) NA(n->dy[L], lp[L] * kNet[L].cout);
