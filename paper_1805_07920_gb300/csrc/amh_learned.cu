@@ -46,22 +46,53 @@ struct LayerDef { int cin, cout, relu; };
 constexpr LayerDef kNet[kLayers] = {{16, 32, 1}, {32, 64, 1}, {64, 96, 1}, {96, 128, 1},
                                     {128, 96, 1}, {96, 64, 1}, {64, 32, 1}, {32, 16, 0}};
 
-// bias gradient in FP32: db[c] = sum over pixels of dy(p, c)
+// bias gradient in FP32: db[c] += sum over pixels of dy(p, c), C a multiple
+// of 16 (at most 128), in two passes without atomics.  Pass 1: a thread sums
+// four channels (one float4) of every k-th pixel of its block's range,
+// k = 256 / (C / 4), and the block writes its per-channel sums to part[block].
+// Pass 2: one block per channel adds the partial sums into db.
+constexpr int kBiasBlocks = 2048;     // most pass-1 blocks (rows of the partial sums)
 __global__ void __launch_bounds__(256) bias_grad_kernel(const float* __restrict__ dy, int np, int C,
-                                                        int per_block, float* db) {
-  __shared__ float red[8][33];
-  const int c = blockIdx.x * 32 + (threadIdx.x & 31), r = threadIdx.x >> 5;
-  const int p0 = blockIdx.y * per_block, p1 = min(np, p0 + per_block);
-  float s = 0.f;
-  if (c < C)
-    for (int p = p0 + r; p < p1; p += 8) s += dy[(size_t)p * C + c];
-  red[r][threadIdx.x & 31] = s;
-  __syncthreads();
-  if (r == 0) {
-    float tot = 0.f;
-    for (int q = 0; q < 8; q++) tot += red[q][threadIdx.x & 31];
-    if (c < C) atomicAdd(&db[c], tot);
+                                                        int per_block, float* __restrict__ part) {
+  __shared__ float4 red[256];
+  const int g4 = C >> 2, k = 256 / g4, t = threadIdx.x, g = t % g4, j = t / g4;
+  const int p0 = blockIdx.x * per_block, p1 = min(np, p0 + per_block);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (j < k) {
+#pragma unroll 4
+    for (int p = p0 + j; p < p1; p += k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(dy + (size_t)p * C) + g);
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
   }
+  red[t] = s;
+  __syncthreads();
+  if (j == 0) {
+    for (int q = 1; q < k; q++) {
+      const float4 v = red[q * g4 + g];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    reinterpret_cast<float4*>(part + (size_t)blockIdx.x * C)[g] = s;
+  }
+}
+__global__ void __launch_bounds__(256) bias_sum_kernel(const float* __restrict__ part, int nb, int C, float* db) {
+  __shared__ float red[256];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < nb; b += 256) s += part[(size_t)b * C + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] += red[0];
 }
 
 // weights (9, Cout, Cin) -> data-gradient weights (9, Cin, Cout), taps flipped
@@ -73,46 +104,72 @@ __global__ void flip_transpose_kernel(const __nv_bfloat16* w, __nv_bfloat16* wd,
   }
 }
 
-__global__ void pool2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int H, int W, int C) {
+// The elementwise kernels below take four channels per thread and step (C is
+// a multiple of 16, so a group of four never crosses a pixel): 16-byte FP32
+// and 8-byte BF16 accesses.
+struct bf16x4 { __nv_bfloat162 a, b; };
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+  const bf16x4 v = *reinterpret_cast<const bf16x4*>(p);
+  const float2 lo = __bfloat1622float2(v.a), hi = __bfloat1622float2(v.b);
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
+  bf16x4 o;
+  o.a = __floats2bfloat162_rn(v.x, v.y);
+  o.b = __floats2bfloat162_rn(v.z, v.w);
+  *reinterpret_cast<bf16x4*>(p) = o;
+}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+
+__global__ void pool2_kernel(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int H, int W, int C) {
   const int Ho = H / 2, Wo = W / 2;
-  const size_t n = (size_t)Ho * Wo * C;
+  const size_t n = (size_t)Ho * Wo * C / 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C, p = (int)(i / C), oy = p / Wo, ox = p % Wo;
+    const int c = (int)(4 * i % C), p = (int)(4 * i / C), oy = p / Wo, ox = p % Wo;
     const size_t b = ((size_t)(2 * oy) * W + 2 * ox) * C + c;
-    const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (size_t)W * C]) +
-                    __bfloat162float(x[b + (size_t)W * C + C]);
-    y[i] = __float2bfloat16(0.25f * s);
+    const float4 s = add4(add4(add4(ld4(x + b), ld4(x + b + C)), ld4(x + b + (size_t)W * C)), ld4(x + b + (size_t)W * C + C));
+    st4(y + 4 * i, scale4(0.25f, s));
   }
 }
-__global__ void pool2_bwd_add_kernel(const float* d, float* dx, int H, int W, int C) {   // dx += pool'^T d
-  const size_t n = (size_t)H * W * C;
+__global__ void pool2_bwd_add_kernel(const float* __restrict__ d, float* __restrict__ dx, int H, int W, int C) {   // dx += pool'^T d
+  const size_t n = (size_t)H * W * C / 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C, p = (int)(i / C), yy = p / W, xx = p % W;
-    dx[i] += 0.25f * d[((size_t)(yy / 2) * (W / 2) + xx / 2) * C + c];
+    const int c = (int)(4 * i % C), p = (int)(4 * i / C), yy = p / W, xx = p % W;
+    float4* o = reinterpret_cast<float4*>(dx) + i;
+    *o = add4(*o, scale4(0.25f, *reinterpret_cast<const float4*>(d + ((size_t)(yy / 2) * (W / 2) + xx / 2) * C + c)));
   }
 }
-__global__ void up2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int Ho, int Wo, int C) {  // (Ho, Wo) output
-  const size_t n = (size_t)Ho * Wo * C;
+__global__ void up2_kernel(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int Ho, int Wo, int C) {  // (Ho, Wo) output
+  const size_t n = (size_t)Ho * Wo * C / 4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C, p = (int)(i / C), yy = p / Wo, xx = p % Wo;
-    y[i] = x[((size_t)(yy / 2) * (Wo / 2) + xx / 2) * C + c];
+    const int c = (int)(4 * i % C), p = (int)(4 * i / C), yy = p / Wo, xx = p % Wo;
+    *reinterpret_cast<bf16x4*>(y + 4 * i) =
+        *reinterpret_cast<const bf16x4*>(x + ((size_t)(yy / 2) * (Wo / 2) + xx / 2) * C + c);
   }
 }
-__global__ void up2_bwd_kernel(const float* d, float* dx, int H, int W, int C) {   // (H, W) = input size
-  const size_t n = (size_t)H * W * C;
+__global__ void up2_bwd_kernel(const float* __restrict__ d, float* __restrict__ dx, int H, int W, int C) {   // (H, W) = input size
+  const size_t n = (size_t)H * W * C / 4;
   const int Wo = 2 * W;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C, p = (int)(i / C), yy = p / W, xx = p % W;
-    const size_t b = ((size_t)(2 * yy) * Wo + 2 * xx) * C + c;
-    dx[i] = d[b] + d[b + C] + d[b + (size_t)Wo * C] + d[b + (size_t)Wo * C + C];
+    const int c = (int)(4 * i % C), p = (int)(4 * i / C), yy = p / W, xx = p % W;
+    const float* b = d + ((size_t)(2 * yy) * Wo + 2 * xx) * C + c;
+    const float4 s = add4(add4(add4(*reinterpret_cast<const float4*>(b), *reinterpret_cast<const float4*>(b + C)),
+                               *reinterpret_cast<const float4*>(b + (size_t)Wo * C)),
+                          *reinterpret_cast<const float4*>(b + (size_t)Wo * C + C));
+    reinterpret_cast<float4*>(dx)[i] = s;
   }
 }
-// g (FP32) times the ReLU mask of r, optionally also into a BF16 copy
-__global__ void relu_mask_kernel(const float* g, const __nv_bfloat16* r, float* out, __nv_bfloat16* out16, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float v = __bfloat162float(r[i]) > 0.f ? g[i] : 0.f;
-    out[i] = v;
-    if (out16) out16[i] = __float2bfloat16(v);
+// g (FP32) times the ReLU mask of r, optionally also into a BF16 copy; n a
+// multiple of 4
+__global__ void relu_mask_kernel(const float* __restrict__ g, const __nv_bfloat16* __restrict__ r, float* __restrict__ out,
+                                 __nv_bfloat16* __restrict__ out16, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 gv = reinterpret_cast<const float4*>(g)[i], rv = ld4(r + 4 * i);
+    const float4 v = make_float4(rv.x > 0.f ? gv.x : 0.f, rv.y > 0.f ? gv.y : 0.f, rv.z > 0.f ? gv.z : 0.f,
+                                 rv.w > 0.f ? gv.w : 0.f);
+    reinterpret_cast<float4*>(out)[i] = v;
+    if (out16) st4(out16 + 4 * i, v);
   }
 }
 __global__ void bf16_to_f32_kernel(const __nv_bfloat16* g, float* o, size_t n) {
@@ -125,20 +182,29 @@ __global__ void to_bf16_kernel(const float* g, __nv_bfloat16* o, size_t n) {
 }
 
 // L1 loss over the 4 used output channels of the masked pixels and its
-// gradient; loss accumulated in *loss (sum; the host divides by the count)
-__global__ void l1_loss_kernel(const float* out, const float* target, const uint8_t* mask, float* dout, float* loss,
-                               int np, float inv_n) {
+// gradient (zero on the other 12 channels); loss accumulated in *loss (sum;
+// the host divides by the count)
+__global__ void l1_loss_kernel(const float* __restrict__ out, const float* __restrict__ target,
+                               const uint8_t* __restrict__ mask, float* __restrict__ dout, float* loss, int np,
+                               float inv_n) {
   float s = 0.f;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    for (int c = 0; c < 16; c++) {
-      float g = 0.f;
-      if (c < 4 && mask[p]) {
-        const float d = out[(size_t)p * 16 + c] - target[(size_t)p * 4 + c];
-        s += fabsf(d);
-        g = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * inv_n;
+    const float4 o = reinterpret_cast<const float4*>(out)[(size_t)p * 4];
+    const float4 t = reinterpret_cast<const float4*>(target)[p];
+    const bool on = mask[p] != 0;
+    const float d[4] = {o.x - t.x, o.y - t.y, o.z - t.z, o.w - t.w};
+    float g[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      g[c] = 0.f;
+      if (on) {
+        s += fabsf(d[c]);
+        g[c] = (d[c] > 0.f ? 1.f : (d[c] < 0.f ? -1.f : 0.f)) * inv_n;
       }
-      dout[(size_t)p * 16 + c] = g;
     }
+    float4* dp = reinterpret_cast<float4*>(dout) + (size_t)p * 4;
+    dp[0] = make_float4(g[0], g[1], g[2], g[3]);
+    dp[1] = dp[2] = dp[3] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_n);
@@ -189,16 +255,19 @@ __global__ void example_kernel(const float* __restrict__ x, int C, const float* 
     const int X = p % w2, Y = p / w2;
     const int sx = (mirror & 1) ? w2 - 1 - X : X, sy = (mirror & 2) ? h2 - 1 - Y : Y;
     const size_t q = (size_t)sy * w2 + sx;
+    __align__(16) __nv_bfloat16 row[16];
+#pragma unroll
     for (int c = 0; c < 16; c++) {
       float v = c < C ? x[q * C + c] : 0.f;
       if ((c == 2 && (mirror & 1)) || (c == 3 && (mirror & 2))) v = -v;
-      x0[(size_t)p * 16 + c] = __float2bfloat16(v);
+      row[c] = __float2bfloat16(v);
     }
-    for (int c = 0; c < 4; c++) {
-      float v = t[q * 4 + c];
-      if ((c == 1 && (mirror & 1)) || (c == 2 && (mirror & 2))) v = -v;
-      target[(size_t)p * 4 + c] = v;
-    }
+    reinterpret_cast<uint4*>(x0)[(size_t)p * 2] = reinterpret_cast<const uint4*>(row)[0];
+    reinterpret_cast<uint4*>(x0)[(size_t)p * 2 + 1] = reinterpret_cast<const uint4*>(row)[1];
+    float4 tv = reinterpret_cast<const float4*>(t)[q];
+    if (mirror & 1) tv.y = -tv.y;
+    if (mirror & 2) tv.z = -tv.z;
+    reinterpret_cast<float4*>(target)[p] = tv;
     mask[p] = m[q];
   }
 }
@@ -265,6 +334,7 @@ struct amh_net {
   __nv_bfloat16* wd16[kLayers] = {};      // data-gradient weights
   float *mw[kLayers] = {}, *vw[kLayers] = {}, *mb[kLayers] = {}, *vb[kLayers] = {};
   float *gw[kLayers] = {}, *gb[kLayers] = {};
+  float* bpart = nullptr;                 // per-block partial sums of the bias gradients
   int step = 0;
   // activations (BF16) and gradient buffers (FP32)
   __nv_bfloat16 *x0 = nullptr, *e1 = nullptr, *in_e2 = nullptr, *e2 = nullptr, *in_e3 = nullptr, *e3 = nullptr,
@@ -432,8 +502,12 @@ int wgrad(amh_net* n, int L, const __nv_bfloat16* x, const float* dy, const __nv
   const int per_cta = (steps + std::max(1, n_sm / gy) - 1) / std::max(1, n_sm / gy);
   const tc::WgradTcArgs a{n->gw[L], n->status, H, W, Cin, Cout, per_cta, stacked, S};
   tc::wgrad3x3_tc_kernel<<<dim3((steps + per_cta - 1) / per_cta, gy), tc::kThreads, smem, n->stream>>>(mdy, mx, a);
-  const int per_block = 2048, nb = (np + per_block - 1) / per_block;
-  bias_grad_kernel<<<dim3((Cout + 31) / 32, nb), 256, 0, n->stream>>>(dy, np, Cout, per_block, n->gb[L]);
+  // about eight blocks per SM (at most kBiasBlocks), each a whole number of
+  // the block's pixel steps
+  const int step = 256 / (Cout / 4), want = std::min(kBiasBlocks, 8 * n_sm), per = (np + want - 1) / want;
+  const int per_block = std::max(step, (per + step - 1) / step * step), nb = (np + per_block - 1) / per_block;
+  bias_grad_kernel<<<nb, 256, 0, n->stream>>>(dy, np, Cout, per_block, n->bpart);
+  bias_sum_kernel<<<Cout, 256, 0, n->stream>>>(n->bpart, nb, Cout, n->gb[L]);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "wgrad launch: %s", cudaGetErrorString(e));
   return AMH_OK;
@@ -489,6 +563,7 @@ AMH_API int amh_net_create(amh_net** out, int32_t width2, int32_t height2, uint6
     cudaMemcpyAsync(n->wm[L], w.data(), nw * sizeof(float), cudaMemcpyHostToDevice, n->stream);
     cudaStreamSynchronize(n->stream);
   }
+  NA(n->bpart, (size_t)kBiasBlocks * 128);
   NA(n->status, 1);
   const size_t P0 = (size_t)width2 * height2, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
   NA(n->x0, P0 * 16); NA(n->e1, P0 * 32); NA(n->in_e2, P1 * 32); NA(n->e2, P1 * 64); NA(n->in_e3, P2 * 64);
@@ -571,6 +646,10 @@ AMH_API int amh_net_set_example(amh_net* n, const float* x, int32_t channels, co
     dx = n->gA;
     dt = n->gB;
     dm = mb;
+  }
+  if (reinterpret_cast<uintptr_t>(dt) & 15) {   // the kernel reads each pixel's targets as one float4
+    NTRY(n, cudaMemcpyAsync(n->gB, dt, np * 16, cudaMemcpyDeviceToDevice, n->stream));
+    dt = n->gB;
   }
   example_kernel<<<blocks_for(np), 256, 0, n->stream>>>(dx, channels, dt, dm, n->w2, n->h2, mirror & 3, n->x0,
                                                         n->target, n->mask);
