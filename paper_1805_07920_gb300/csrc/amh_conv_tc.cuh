@@ -100,11 +100,29 @@ struct RingPos {
 __host__ __device__ constexpr uint32_t mma_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
+// The MMA warps run their issue loops with all 32 lanes converged, so that
+// the descriptor arithmetic is warp-uniform; one lane chosen by elect.sync
+// (the same lane every time, the warp being converged) issues each MMA and
+// each commit.  Measured: 39-48 cycles per M = 128, K = 16 MMA (N <= 64)
+// with the descriptors computed in the loop this way, 63-68 cycles when a
+// single lane runs the loop.
+__device__ __forceinline__ void mma_bf16_elect(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                               uint32_t accumulate) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+__device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+// a barrier wait by the whole warp, with one answer for all its lanes
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity) {
+  return __all_sync(0xffffffffu, mbar_wait(b, parity));
 }
 // 16 consecutive accumulator columns of this thread's TMEM lane (the warp
 // reads its lane quarter); the caller waits with tcgen05.wait::ld
@@ -115,10 +133,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
 }
 
 // Both kernels are persistent and warp-specialised: epilogue warps drain the
@@ -279,13 +293,13 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
   } else if (warp == w_mma) {
     // MMA issuer: output row i of a run accumulates 9 Cin / 16 MMAs over the
     // slabs i, i + 1, i + 2 of the run into accumulator buffer (tile count % 2)
-    if (lane == 0) {
+    {   // all 32 lanes: warp-uniform descriptors, elected issue
       const uint32_t idesc = mma_idesc(kM, Nb);
       const uint32_t hi_main = desc_hi(128u), hi_tail = desc_hi(2u * (uint32_t)tail);
       const uint32_t w_lo = desc_lo(smem_u32(wsm)), s_lo = desc_lo(smem_u32(slabs));
       const uint32_t wtap16 = wtap_bytes >> 4, slab16 = slab_bytes >> 4, sblk16 = sblk >> 4, wblk16 = wblk >> 4;
       const uint32_t tail16 = (2u * (uint32_t)tail) >> 4;      // the tail's row pitch, in 16-byte units
-      ok = mbar_wait(&wbar, 0);
+      ok = mbar_wait_warp(&wbar, 0);
       uint32_t tc = 0;
       RingPos q{0u, 0u};    // ring position of the next slab
       TileRun r;
@@ -294,9 +308,9 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
         for (int i = 0; i < r.len && ok; i++, tc++) {
           const uint32_t b = tc & 1u;
           const RingPos q2 = q1.next((uint32_t)S);
-          if (!(ok = mbar_wait(&acc_empty[b], ((tc >> 1) & 1u) ^ 1u))) break;
-          if (i == 0) ok = mbar_wait(&full[q0.slot], q0.phase) && mbar_wait(&full[q1.slot], q1.phase);
-          if (!(ok = ok && mbar_wait(&full[q2.slot], q2.phase))) break;
+          if (!(ok = mbar_wait_warp(&acc_empty[b], ((tc >> 1) & 1u) ^ 1u))) break;
+          if (i == 0) ok = mbar_wait_warp(&full[q0.slot], q0.phase) && mbar_wait_warp(&full[q1.slot], q1.phase);
+          if (!(ok = ok && mbar_wait_warp(&full[q2.slot], q2.phase))) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + b * ncols;
           uint32_t acc = 0;
@@ -310,7 +324,7 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
               for (int c = 0; c < 4; c++)
 #pragma unroll
                 for (int dx = 0; dx < 3; dx++) {
-                  mma_bf16(d, desc_pack(xb + 8u * dx + 2u * c, hi_main), desc_pack(wb + dx * wtap16 + 2u * c, hi_main),
+                  mma_bf16_elect(d, desc_pack(xb + 8u * dx + 2u * c, hi_main), desc_pack(wb + dx * wtap16 + 2u * c, hi_main),
                            idesc, acc);
                   acc = 1;
                 }
@@ -320,21 +334,21 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
               for (uint32_t c = 0; c < tail16 / 2; c++)
 #pragma unroll
                 for (int dx = 0; dx < 3; dx++) {
-                  mma_bf16(d, desc_pack(xb + tail16 * dx + 2u * c, hi_tail), desc_pack(wb + dx * wtap16 + 2u * c, hi_tail),
+                  mma_bf16_elect(d, desc_pack(xb + tail16 * dx + 2u * c, hi_tail), desc_pack(wb + dx * wtap16 + 2u * c, hi_tail),
                            idesc, acc);
                   acc = 1;
                 }
             }
           }
-          mma_commit(&acc_full[b]);
-          mma_commit(&empty[q0.slot]);    // slab i is read by no later row
+          mma_commit_elect(&acc_full[b]);
+          mma_commit_elect(&empty[q0.slot]);    // slab i is read by no later row
           q0 = q1;
           q1 = q2;
         }
         if (!ok) break;
         // the run's last two slabs
-        mma_commit(&empty[q0.slot]);
-        mma_commit(&empty[q1.slot]);
+        mma_commit_elect(&empty[q0.slot]);
+        mma_commit_elect(&empty[q1.slot]);
         q = q1.next((uint32_t)S);
       }
     }
@@ -522,7 +536,7 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_tc_kernel(const __grid_cons
       }
     }
   } else if (warp == 5) {
-    if (lane == 0) {
+    {   // all 32 lanes: warp-uniform descriptors, elected issue
       const uint32_t idesc = mma_idesc(kM, a.Cin) | (1u << 15) | (1u << 16);   // A and B MN-major
       const uint32_t a_hi = desc_hi(2u * (uint32_t)cba), b_hi = desc_hi(2u * (uint32_t)cbb);
       const uint32_t a_lo = desc_lo_mn(smem_u32(ring), 128u * (uint32_t)cba);
@@ -532,18 +546,18 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_tc_kernel(const __grid_cons
       const uint32_t stage16 = stage_bytes >> 4;
       RingPos q{0u, 0u};
       for (int k = 0; k < nk && ok; k++, q = q.next((uint32_t)S)) {
-        if (!(ok = mbar_wait(&full[q.slot], q.phase))) break;
+        if (!(ok = mbar_wait_warp(&full[q.slot], q.phase))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 4; c++)
 #pragma unroll
           for (int dx = 0; dx < 3; dx++)
-            mma_bf16(tmem + (uint32_t)dx * stride, desc_pack(a_lo + q.slot * stage16 + 16u * a_row * c, a_hi),
+            mma_bf16_elect(tmem + (uint32_t)dx * stride, desc_pack(a_lo + q.slot * stage16 + 16u * a_row * c, a_hi),
                      desc_pack(b_lo + q.slot * stage16 + (16u * c + (uint32_t)dx) * b_row, b_hi), idesc,
                      (k > 0 || c > 0) ? 1u : 0u);
-        mma_commit(&empty[q.slot]);
+        mma_commit_elect(&empty[q.slot]);
       }
-      if (ok) mma_commit(&acc_full);
+      if (ok) mma_commit_elect(&acc_full);
     }
   } else if (nk > 0) {
     // epilogue: TMEM lane 32 w + l is A's row: (vertical tap w - 1, output
