@@ -67,21 +67,19 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
-// shared-memory matrix descriptor, K-major: start address, leading byte
-// offset (without swizzling: between the two 8-element core matrices along
-// K), stride byte offset (between 8-row groups along M / N), descriptor
-// version 1, base offset 0 and the layout type in bits 61-63 (0: no swizzle;
-// 2, 4, 6: rows of 128, 64, 32 bytes with the matching swizzle, whose pattern
-// follows the shared-memory address bits, so a start moved by whole rows
-// stays consistent with what the TMA wrote)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7u) << 61);
-}
+// Shared-memory matrix descriptor of a tcgen05 operand, as two 32-bit words.
+// Low word: start address >> 4 (bits 0-13) and the leading byte offset >> 4
+// (bits 16-29; ignored for swizzled K-major operands, set to 16 bytes;
+// for MN-major operands the step between blocks along M / N, see
+// desc_lo_mn).  High word: the stride byte offset >> 4 (between 8-row groups:
+// along M / N for K-major, along K for MN-major; 8 rows of `pitch` bytes
+// either way), descriptor version 1 (bit 46 of the whole), base offset 0 and
+// the layout in bits 61-63 (2, 4, 6: rows of 128, 64, 32 bytes with the
+// matching swizzle).  The swizzle pattern follows the shared-memory address
+// bits, so a start moved by whole rows stays consistent with what the TMA
+// wrote.  The low word moves with the operand; the high word is fixed per
+// channel block.
 __host__ __device__ constexpr uint32_t swizzle_layout(int pitch) { return pitch == 128 ? 2u : pitch == 64 ? 4u : 6u; }
-// the same descriptor as two 32-bit words: the low one (start >> 4, leading
-// byte offset 16) moves with the operand, the high one (stride 8 rows of
-// `pitch` bytes, version, swizzle) is fixed per channel block
 __device__ __forceinline__ uint32_t desc_lo(uint32_t addr) { return ((addr >> 4) & 0x3FFFu) | (1u << 16); }
 __device__ __forceinline__ uint32_t desc_hi(uint32_t pitch) {
   return ((8u * pitch) >> 4) | (1u << 14) | (swizzle_layout((int)pitch) << 29);
