@@ -147,6 +147,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
+// Store one 32-byte sector per pixel (16 BF16 or 8 FP32 channels, as two
+// 16-byte halves lo, hi) for the pixels of lane pairs (2k, 2k + 1), which
+// are neighbours, so that each store instruction writes whole sectors: the
+// first writes the even pixel's sector (its lo from the even lane, its hi
+// from the odd one), the second the odd pixel's.  self / partner point at
+// this lane's and the pair partner's sector; st_self / st_partner say
+// whether those pixels are stored.  All 32 lanes call it together.
+__device__ __forceinline__ void store_sector_pair(uint4* self, uint4* partner, uint4 lo, uint4 hi, bool odd,
+                                                  bool st_self, bool st_partner) {
+  const uint4 send = odd ? lo : hi;    // the half the partner stores for this lane's pixel
+  uint4 recv;
+  recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+  recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+  recv.z = __shfl_xor_sync(0xffffffffu, send.z, 1);
+  recv.w = __shfl_xor_sync(0xffffffffu, send.w, 1);
+  uint4* const pa = odd ? partner + 1 : self;      // the even pixel's sector
+  uint4* const pb = odd ? self + 1 : partner;      // the odd pixel's sector
+  const uint4 va = odd ? recv : lo, vb = odd ? hi : recv;
+  const bool sa = odd ? st_partner : st_self, sb = odd ? st_self : st_partner;
+  if (sa) *pa = va;
+  if (sb) *pb = vb;
+}
+
 // Forward / data-gradient kernel.  A tile is 128 consecutive pixels of one
 // output row and one block of Nb output channels; CTA (bx, by) owns channel
 // block by and a contiguous range of the tiles ordered (128-pixel column
@@ -219,6 +242,11 @@ __device__ __forceinline__ bool next_run(int& u, int hi, int H, TileRun& r) {
 // tx_main / tw_main: boxes of 64 channels x (kHalo pixels | Nb output
 // channels), 128-byte swizzle; tx_tail / tw_tail: the same for the tail
 // channels (unused when Cin is a multiple of 64)
+// kPairStores: the epilogue writes whole 32-byte sectors through lane pairs
+// (store_sector_pair); it pays where the stores bound the layer (the decoder
+// layers with a skip input and two BF16 outputs) and costs registers and
+// shuffles elsewhere
+template <bool kPairStores>
 __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tx_main,
                                                               const __grid_constant__ CUtensorMap tx_tail,
                                                               const __grid_constant__ CUtensorMap tw_main,
@@ -378,7 +406,16 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[b]);
-        if (!in) continue;
+        if (!kPairStores && !in) continue;
+        // with paired stores every lane goes on (the stores pair neighbouring
+        // lanes); lanes past the row's end compute on their TMEM rows and
+        // store only their partner's pixel
+        const bool odd = (lane & 1) != 0;
+        const bool in_partner = kPairStores ? __shfl_xor_sync(0xffffffffu, in ? 1 : 0, 1) != 0 : false;
+        const ptrdiff_t po = odd ? -(ptrdiff_t)a.Cout : (ptrdiff_t)a.Cout;   // the partner pixel's offset
+        // store offsets from the unclamped pixel (px - 1 <= W - 1 for the
+        // partner of a lane past the row's end)
+        const size_t os = ((size_t)y * a.W + px) * a.Cout + co0 + c0;
         float f[16];
 #pragma unroll
         for (int e = 0; e < 16; e++) {
@@ -389,8 +426,14 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
         if (a.r16) {
 #pragma unroll
           for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
-          reinterpret_cast<uint4*>(a.r16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
-          reinterpret_cast<uint4*>(a.r16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+          if constexpr (kPairStores) {
+            store_sector_pair(reinterpret_cast<uint4*>(a.r16 + os), reinterpret_cast<uint4*>(a.r16 + os + po),
+                              reinterpret_cast<const uint4*>(hb)[0], reinterpret_cast<const uint4*>(hb)[1], odd, in,
+                              in_partner);
+          } else {
+            reinterpret_cast<uint4*>(a.r16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
+            reinterpret_cast<uint4*>(a.r16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+          }
         }
         if (a.skip) {
           __align__(16) __nv_bfloat16 skb[16];
@@ -402,13 +445,30 @@ __global__ void __launch_bounds__(kConvMaxThreads, 1) conv3x3_tc_kernel(const __
         if (a.y16) {
 #pragma unroll
           for (int e = 0; e < 16; e++) hb[e] = __float2bfloat16(f[e]);
-          reinterpret_cast<uint4*>(a.y16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
-          reinterpret_cast<uint4*>(a.y16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+          if constexpr (kPairStores) {
+            store_sector_pair(reinterpret_cast<uint4*>(a.y16 + os), reinterpret_cast<uint4*>(a.y16 + os + po),
+                              reinterpret_cast<const uint4*>(hb)[0], reinterpret_cast<const uint4*>(hb)[1], odd, in,
+                              in_partner);
+          } else {
+            reinterpret_cast<uint4*>(a.y16 + o)[0] = reinterpret_cast<const uint4*>(hb)[0];
+            reinterpret_cast<uint4*>(a.y16 + o)[1] = reinterpret_cast<const uint4*>(hb)[1];
+          }
         }
-        if (a.y32) {
+        if (a.y32 && !kPairStores) {
           float4* q4 = reinterpret_cast<float4*>(a.y32 + o);
 #pragma unroll
           for (int e = 0; e < 4; e++) q4[e] = make_float4(f[4 * e], f[4 * e + 1], f[4 * e + 2], f[4 * e + 3]);
+        }
+        if (a.y32 && kPairStores) {   // two sectors: channels 0-7 and 8-15
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const uint4 lo = make_uint4(__float_as_uint(f[8 * h]), __float_as_uint(f[8 * h + 1]),
+                                        __float_as_uint(f[8 * h + 2]), __float_as_uint(f[8 * h + 3]));
+            const uint4 hi = make_uint4(__float_as_uint(f[8 * h + 4]), __float_as_uint(f[8 * h + 5]),
+                                        __float_as_uint(f[8 * h + 6]), __float_as_uint(f[8 * h + 7]));
+            store_sector_pair(reinterpret_cast<uint4*>(a.y32 + os + 8 * h), reinterpret_cast<uint4*>(a.y32 + os + po + 8 * h),
+                              lo, hi, odd, in, in_partner);
+          }
         }
       }
     }

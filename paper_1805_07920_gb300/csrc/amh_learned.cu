@@ -447,26 +447,37 @@ int conv(amh_net* n, const __nv_bfloat16* x, const __nv_bfloat16* w, const float
   int dev = 0;
   cudaGetDevice(&dev);
   if (!n_sm[dev & 63]) cudaDeviceGetAttribute(&n_sm[dev & 63], cudaDevAttrMultiProcessorCount, dev);
+  // the decoder layers (skip input, two BF16 outputs) write their outputs
+  // in whole sectors through lane pairs (tc::store_sector_pair)
+  const int pair = skip ? 1 : 0;
   static std::once_flag once[64];
   static cudaError_t attr_err[64] = {};
-  static int regs[64] = {};
+  static int regs[64][2] = {};
   std::call_once(once[dev & 63], [dev] {
-    attr_err[dev & 63] = cudaFuncSetAttribute(tc::conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)tc::kConvSmemCap);
+    cudaError_t e = cudaSuccess;
     cudaFuncAttributes fa;
-    if (attr_err[dev & 63] == cudaSuccess) attr_err[dev & 63] = cudaFuncGetAttributes(&fa, tc::conv3x3_tc_kernel);
-    if (attr_err[dev & 63] == cudaSuccess) regs[dev & 63] = fa.numRegs;
+    const void* kerns[2] = {reinterpret_cast<const void*>(tc::conv3x3_tc_kernel<false>),
+                            reinterpret_cast<const void*>(tc::conv3x3_tc_kernel<true>)};
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+      e = cudaFuncSetAttribute(kerns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kConvSmemCap);
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kerns[k]);
+      if (e == cudaSuccess) regs[dev & 63][k] = fa.numRegs;
+    }
+    attr_err[dev & 63] = e;
   });
   if (attr_err[dev & 63] != cudaSuccess)
     return nfail(n, AMH_ECUDA, "conv: shared-memory attribute: %s", cudaGetErrorString(attr_err[dev & 63]));
   if (p.smem > tc::kConvSmemCap) return nfail(n, AMH_EINVAL, "conv: shared memory plan too large");
   // CTAs resident per SM: the plan's, and what the register file holds
   const int threads = tc::conv_threads(p.Nb);
-  const int by_regs = 65536 / (((regs[dev & 63] + 7) & ~7) * threads);
+  const int by_regs = 65536 / (((regs[dev & 63][pair] + 7) & ~7) * threads);
   const int cps = std::max(1, std::min(p.ctas_per_sm, by_regs));
   const int nblk = Cout / p.Nb, ntiles = H * ((W + tc::kM - 1) / tc::kM);
   const int gx = std::max(1, std::min(ntiles, n_sm[dev & 63] * cps / nblk));
-  tc::conv3x3_tc_kernel<<<dim3(gx, nblk), threads, p.smem, n->stream>>>(mx[0], mx[1], mw[0], mw[1], a);
+  if (pair)
+    tc::conv3x3_tc_kernel<true><<<dim3(gx, nblk), threads, p.smem, n->stream>>>(mx[0], mx[1], mw[0], mw[1], a);
+  else
+    tc::conv3x3_tc_kernel<false><<<dim3(gx, nblk), threads, p.smem, n->stream>>>(mx[0], mx[1], mw[0], mw[1], a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(n, AMH_ECUDA, "conv launch: %s", cudaGetErrorString(e));
   return AMH_OK;
